@@ -1,0 +1,125 @@
+/*
+ * mqntt.h -- multi-word modular NTT and BLAS on one GB300 (sm_103a): the C ABI.
+ *
+ * The library computes the two data-parallel kernels of "Towards Closing the Performance Gap for
+ * Cryptographic Kernels Between CPUs and Specialized Hardware" (Zhang, Fu, Franchetti, MICRO '25)
+ * over 64-bit and 128-bit residues:
+ *   - modular BLAS (Sec. 2.3, point-wise polynomial operations): vector add, vector subtract,
+ *     point-wise vector multiply and axpy y = a x + y, all mod q;
+ *   - the number theoretic transform (Sec. 2.3, Eq. 4) and its inverse, negacyclic (x^N + 1) by
+ *     default or cyclic (x^N - 1).
+ * Every result is the exact canonical residue in [0, q): the arithmetic is integer only.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: MQ_OK (0) or a negative MQ_ERR_* code.  A thread-local
+ *     message describing the last failure is available from mq_last_error().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Compute calls
+ *     are asynchronous on that stream; errors of earlier asynchronous work surface at a later call.
+ *   - Residues: width MQ_W64 stores one residue per 64-bit word (q < 2^60); width MQ_W128 stores one
+ *     residue per two 64-bit words, low word first (the memory image of an unsigned 128-bit
+ *     integer; q < 2^124, the 124-bit bound of Sec. 2.1 that keeps Barrett's constant in range).
+ *     Moduli and scalars are passed as two 64-bit words, low first; for MQ_W64 the high word
+ *     must be 0.
+ *   - q must be odd and at least 3.  Primality is the caller's responsibility for the NTT (the
+ *     plan checks the root's order, which needs a field to mean anything); the BLAS ops are exact
+ *     for any odd q.
+ *   - Inputs must be canonical (< q); non-canonical inputs give unspecified (but memory-safe)
+ *     results.
+ *   - Device pointers are caller-owned device memory (for example torch tensors) and must be
+ *     aligned to the residue size (8 or 16 bytes); MQ_ERR_ALIGN otherwise.
+ */
+#ifndef MQNTT_H
+#define MQNTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MQ_OK 0
+#define MQ_ERR_ARG (-1)      /* null pointer, bad width, bad flag, size overflow */
+#define MQ_ERR_MODULUS (-2)  /* q even, q < 3, too wide for the width, or not 1 mod (2)N */
+#define MQ_ERR_ROOT (-3)     /* root not < q or not of the exact order the transform needs */
+#define MQ_ERR_SIZE (-4)     /* log2 N outside [1, 24], or a stride shorter than N */
+#define MQ_ERR_ALIGN (-5)    /* a device pointer not aligned to the residue size */
+#define MQ_ERR_OOM (-6)      /* device memory allocation failed */
+#define MQ_ERR_CUDA (-7)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define MQ_ERR_TIMEOUT (-8)  /* a bounded device-side wait gave up */
+#define MQ_ERR_RANGE (-9)    /* an input residue was not canonical (checked modes only) */
+#define MQ_ERR_STATE (-10)   /* object in the wrong state for the call */
+
+/* residue widths */
+#define MQ_W64 1  /* uint64_t residues, q < 2^60 */
+#define MQ_W128 2 /* {lo, hi} uint64_t pairs, q < 2^124 */
+
+/* plan flags */
+#define MQ_NEGACYCLIC 0u    /* modulus x^N + 1; root = psi, a primitive 2N-th root of unity */
+#define MQ_CYCLIC 1u        /* modulus x^N - 1 (Eq. 4); root = w, a primitive N-th root of unity */
+#define MQ_ORDER_NATURAL 0u /* transformed side in natural order: position k holds yhat_k */
+#define MQ_ORDER_BITREV 2u  /* transformed side in bit-reversed order: position i holds yhat_brv(i) */
+
+typedef struct ntt_plan ntt_plan;
+
+/*
+ * Create a transform plan for N = 2^log2n residues mod q (Sec. 2.3, Eq. 4).
+ *   negacyclic (default): yhat_k = sum_j x_j psi^((2k+1) j) mod q, q = 1 mod 2N, root = psi with
+ *                         psi^N = -1 (order exactly 2N);
+ *   cyclic:               y_k = sum_j x_j w^(jk) mod q, q = 1 mod N, root = w with w^(N/2) = -1.
+ * The plan validates q and the root's exact order, then builds device-resident twiddle tables
+ * (N entries per direction, each a power of the root and its Shoup companion) on `stream`; the
+ * call returns after they are built.  `q` and `root` are two words each, low first.
+ * log2n in [1, 24].  The plan owns its device memory until ntt_plan_destroy.
+ * Errors: MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
+ */
+int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[2], const uint64_t root[2], int width,
+                    unsigned flags, void *stream);
+
+/* Free a plan (synchronises with the device first).  NULL is accepted. */
+int ntt_plan_destroy(ntt_plan *plan);
+
+/*
+ * In-place forward transform of `batch` polynomials; polynomial b starts at residue b * stride
+ * of d_data (stride >= N when batch > 1).  Input in natural coefficient order; output in the
+ * plan's order.  batch == 0 is a no-op.  Natural-order transforms with N > 2^12 stage through a
+ * temporary device buffer of batch * N residues taken from the library's stream-ordered pool.
+ * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
+ */
+int ntt_forward(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
+
+/*
+ * In-place inverse transform (with the factor N^-1, so that ntt_inverse(ntt_forward(x)) = x).
+ * Input in the plan's order, output in natural coefficient order.  Same arguments and errors as
+ * ntt_forward.
+ */
+int ntt_inverse(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
+
+/* Plan properties (for callers that size buffers from a plan). */
+int ntt_plan_info(const ntt_plan *plan, unsigned *log2n, int *width, unsigned *flags);
+
+/*
+ * Element-wise modular BLAS over n residues (Sec. 2.3; modular ring operations of Sec. 2.1, Eq. 1).
+ *   mod_vadd: c_i = a_i + b_i mod q      mod_vsub: c_i = a_i - b_i mod q
+ *   mod_vmul: c_i = a_i * b_i mod q      mod_axpy: y_i = a * x_i + y_i mod q (scalar a < q)
+ * Any n (0 is a no-op).  The output may alias any input.  Errors: MQ_ERR_ARG, MQ_ERR_MODULUS,
+ * MQ_ERR_ALIGN, MQ_ERR_CUDA.
+ */
+int mod_vadd(void *d_c, const void *d_a, const void *d_b, size_t n, const uint64_t q[2], int width, void *stream);
+int mod_vsub(void *d_c, const void *d_a, const void *d_b, size_t n, const uint64_t q[2], int width, void *stream);
+int mod_vmul(void *d_c, const void *d_a, const void *d_b, size_t n, const uint64_t q[2], int width, void *stream);
+int mod_axpy(void *d_y, const uint64_t a[2], const void *d_x, size_t n, const uint64_t q[2], int width,
+             void *stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *mq_last_error(void);
+
+/* Library version string. */
+const char *mq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MQNTT_H */

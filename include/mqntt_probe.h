@@ -1,0 +1,33 @@
+/*
+ * mqntt_probe.h -- measurement probes for the roofline of the modular kernels.
+ *
+ * The paper locates the cost of 128-bit modular arithmetic in word multiplies and carries
+ * (Sec. 4: the widening multiply and add-with-carry are the missing AVX-512 pieces; Sec. 5.3:
+ * widening multiply matters most).  On the GPU these are 32-bit multiply-add instructions
+ * (mad.lo / mad.hi, with carry-chained variants), so the compute roof of the transforms is the
+ * device's issue rate of those instructions.  This probe measures it; it is not a published figure.
+ */
+#ifndef MQNTT_PROBE_H
+#define MQNTT_PROBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MQ_PROBE_MAD_LO 0 /* independent mad.lo.u32 chains */
+#define MQ_PROBE_MAD_HI 1 /* independent mad.hi.u32 chains */
+#define MQ_PROBE_MAD_CC 2 /* carry-chained mad.lo.cc / madc.hi.cc pairs */
+
+/*
+ * Run `iters` loop iterations of the chosen multiply-add pattern on every SM (one full wave of
+ * resident CTAs), timed with CUDA events on `stream` (a cudaStream_t; synchronises it).
+ * Writes the aggregate rate in thread-instructions per second to *inst_per_s and the kernel
+ * time to *ms (may be NULL).  Returns 0, or a negative MQ_ERR_* code (see mqntt.h).
+ */
+int mq_probe_imad_rate(int kind, int iters, double *inst_per_s, double *ms, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MQNTT_PROBE_H */

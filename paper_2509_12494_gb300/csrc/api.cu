@@ -1,0 +1,349 @@
+// api.cu -- the C ABI of include/mqntt.h: argument checks, plans, pass scheduling, BLAS dispatch.
+//
+// Host-side scalar precomputation (Barrett constants, Shoup companions of scalars, the inverse
+// root, N^-1) uses unsigned __int128 and binary long division; the per-residue work -- twiddle
+// tables, transforms, BLAS -- runs in the kernels of ntt.cu and blas.cu.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/mqntt.h"
+#include "common.cuh"
+#include "hostmath.h"
+
+using namespace mq;
+
+// ------------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------------
+
+static thread_local char g_err[512];
+
+int mq_fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int mq_cuda_fail(cudaError_t e, const char *where) {
+    return mq_fail(MQ_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+extern "C" const char *mq_last_error(void) { return g_err; }
+extern "C" const char *mq_version(void) { return "mqntt 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------------------------------------
+// modulus checks shared by the BLAS and the plans
+// ------------------------------------------------------------------------------------------------
+
+int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv) {
+    if (!q) return mq_fail(MQ_ERR_ARG, "q is NULL");
+    if (width != MQ_W64 && width != MQ_W128) return mq_fail(MQ_ERR_ARG, "width must be MQ_W64 or MQ_W128, got %d", width);
+    hm::u128 v = hm::from_words(q);
+    if (v < 3 || (v & 1) == 0) return mq_fail(MQ_ERR_MODULUS, "q must be odd and >= 3");
+    if (width == MQ_W64 && (q[1] != 0 || hm::bitlen(v) > 60)) return mq_fail(MQ_ERR_MODULUS, "MQ_W64 needs q < 2^60");
+    if (width == MQ_W128 && hm::bitlen(v) > 124) return mq_fail(MQ_ERR_MODULUS, "MQ_W128 needs q < 2^124");
+    *qv = v;
+    return MQ_OK;
+}
+
+static int check_ptr(const void *p, int width, const char *name) {
+    if (!p) return mq_fail(MQ_ERR_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) % (8u * (unsigned)width)) return mq_fail(MQ_ERR_ALIGN, "%s is not %d-byte aligned", name, 8 * width);
+    return MQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// stream-ordered scratch pool (one per device, created on first use, memory kept cached)
+// ------------------------------------------------------------------------------------------------
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+static bool g_pool_ok[64];
+
+int mq_pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return mq_fail(MQ_ERR_ARG, "device index %d out of range", dev);
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool_ok[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof props);
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pool[dev], &props);
+            if (e != cudaSuccess) return mq_cuda_fail(e, "cudaMemPoolCreate");
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pool_ok[dev] = true;
+        }
+    }
+    e = cudaMallocFromPoolAsync(p, bytes, g_pool[dev], s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return mq_fail(MQ_ERR_OOM, "scratch allocation of %zu bytes failed", bytes);
+    }
+    if (e != cudaSuccess) return mq_cuda_fail(e, "cudaMallocFromPoolAsync");
+    return MQ_OK;
+}
+
+int mq_pool_free(void *p, cudaStream_t s) {
+    cudaError_t e = cudaFreeAsync(p, s);
+    return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "cudaFreeAsync");
+}
+
+// ------------------------------------------------------------------------------------------------
+// plans
+// ------------------------------------------------------------------------------------------------
+
+struct ntt_plan {
+    int device;
+    unsigned log2n;
+    int width;
+    unsigned flags;
+    uint64_t q[2], mu[2];
+    int L;  // bit length of q
+    uint64_t root[2], root_inv[2];
+    void *tw_fwd, *tw_inv;  // N entries of (w, w') each
+    uint64_t sc[2], scp[2], ws[2], wsp[2];
+    int L1;  // rows of the N1 x N2 split (0: single pass)
+};
+
+static int split_of(unsigned log2n) { return log2n <= 12 ? 0 : (int)(log2n / 2); }
+
+extern "C" int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[2], const uint64_t root[2], int width,
+                               unsigned flags, void *stream) {
+    if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!root) return mq_fail(MQ_ERR_ARG, "root is NULL");
+    if (flags & ~(MQ_CYCLIC | MQ_ORDER_BITREV)) return mq_fail(MQ_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (log2n < 1 || log2n > 24) return mq_fail(MQ_ERR_SIZE, "log2n must be in [1, 24], got %u", log2n);
+    hm::u128 Q;
+    int rc = mq_check_modulus(q, width, &Q);
+    if (rc) return rc;
+    const int cyclic = (flags & MQ_CYCLIC) != 0;
+    const hm::u128 N = (hm::u128)1 << log2n;
+    const hm::u128 order = cyclic ? N : 2 * N;
+    if ((Q - 1) % order != 0) return mq_fail(MQ_ERR_MODULUS, "q - 1 is not divisible by %s", cyclic ? "N" : "2N");
+    hm::u128 r = hm::from_words(root);
+    if (r == 0 || r >= Q) return mq_fail(MQ_ERR_ROOT, "root must be in [1, q)");
+    // exact order: psi^N = -1 (order 2N) or w^(N/2) = -1 (order N); orders are powers of two
+    if (hm::powmod(r, order / 2, Q) != Q - 1)
+        return mq_fail(MQ_ERR_ROOT, "root is not a primitive %s root of unity", cyclic ? "N-th" : "2N-th");
+
+    ntt_plan *p = new ntt_plan();
+    memset(p, 0, sizeof *p);
+    cudaGetDevice(&p->device);
+    p->log2n = log2n;
+    p->width = width;
+    p->flags = flags;
+    p->L = hm::bitlen(Q);
+    hm::to_words(Q, p->q);
+    hm::to_words(hm::barrett_mu(Q, p->L), p->mu);
+    hm::to_words(r, p->root);
+    hm::u128 rinv = hm::powmod(r, order - 1, Q);
+    hm::to_words(rinv, p->root_inv);
+    const int B = width == MQ_W64 ? 64 : 128;
+    hm::u128 ninv = Q - (Q - 1) / N;  // N * (q-1)/N = -1 mod q
+    hm::u128 t1 = cyclic ? 1 : hm::powmod(rinv, N / 2, Q);  // inverse-table entry 1
+    hm::u128 ws = hm::mulmod(t1, ninv, Q);
+    hm::to_words(ninv, p->sc);
+    hm::to_words(hm::shoup(ninv, Q, B), p->scp);
+    hm::to_words(ws, p->ws);
+    hm::to_words(hm::shoup(ws, Q, B), p->wsp);
+    p->L1 = split_of(log2n);
+
+    size_t bytes = ((size_t)1 << log2n) * 16u * (size_t)width;
+    cudaError_t e = cudaMalloc(&p->tw_fwd, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tw_inv, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ntt_plan_destroy(p);
+        return mq_fail(MQ_ERR_OOM, "twiddle tables (%zu bytes) do not fit", 2 * bytes);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    e = launch_twiddle_build(width, (int)log2n, cyclic, p->q, p->root, p->root_inv, p->mu, p->L, p->tw_fwd, p->tw_inv, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ntt_plan_destroy(p);
+        return mq_cuda_fail(e, "twiddle build");
+    }
+    *out = p;
+    return MQ_OK;
+}
+
+extern "C" int ntt_plan_destroy(ntt_plan *p) {
+    if (!p) return MQ_OK;
+    cudaDeviceSynchronize();
+    if (p->tw_fwd) cudaFree(p->tw_fwd);
+    if (p->tw_inv) cudaFree(p->tw_inv);
+    delete p;
+    return MQ_OK;
+}
+
+extern "C" int ntt_plan_info(const ntt_plan *p, unsigned *log2n, int *width, unsigned *flags) {
+    if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
+    if (log2n) *log2n = p->log2n;
+    if (width) *width = p->width;
+    if (flags) *flags = p->flags;
+    return MQ_OK;
+}
+
+// Fill the constant part of a pass.
+static PassArgs pass_base(const ntt_plan *p, bool inv, size_t batch) {
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.tw = inv ? p->tw_inv : p->tw_fwd;
+    memcpy(a.q, p->q, sizeof a.q);
+    memcpy(a.sc, p->sc, sizeof a.sc);
+    memcpy(a.scp, p->scp, sizeof a.scp);
+    memcpy(a.ws, p->ws, sizeof a.ws);
+    memcpy(a.wsp, p->wsp, sizeof a.wsp);
+    a.batch = batch;
+    a.logN = (int)p->log2n;
+    a.L1 = p->L1;
+    return a;
+}
+
+static int run_pass(const ntt_plan *p, bool inv, PassArgs &a, int L, cudaStream_t s) {
+    cudaError_t e = launch_ntt_pass(p->width, L, inv, a, s);
+    return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "NTT pass launch");
+}
+
+static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream, bool inv) {
+    if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
+    if (batch == 0) return MQ_OK;
+    int rc = check_ptr(d, p->width, "d_data");
+    if (rc) return rc;
+    const size_t N = (size_t)1 << p->log2n;
+    if (batch == 1) stride = N;
+    if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
+    if (batch > (SIZE_MAX / 16) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool natural = !(p->flags & MQ_ORDER_BITREV);
+    const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
+
+    if (L1 == 0) {  // one pass: the whole transform in one tile
+        PassArgs a = pass_base(p, inv, batch);
+        a.in = a.out = d;
+        a.in_stride = a.out_stride = stride;
+        a.col = 0;
+        a.in_layout = (inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
+        a.out_layout = (!inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
+        a.scale = inv;
+        return run_pass(p, inv, a, logN, s);
+    }
+
+    void *scr = nullptr;
+    if (natural) {
+        rc = mq_pool_alloc(&scr, batch * N * 8u * (size_t)p->width, s);
+        if (rc) return rc;
+    }
+    PassArgs col = pass_base(p, inv, batch), row = pass_base(p, inv, batch);
+    col.col = 1;
+    col.in_layout = col.out_layout = LAYOUT_COL;
+    row.col = 0;
+    if (!inv) {
+        // columns first (stages 0 .. L1-1), then rows
+        col.in = d;
+        col.in_stride = stride;
+        col.out = natural ? scr : d;
+        col.out_stride = natural ? N : stride;
+        row.in = col.out;
+        row.in_stride = col.out_stride;
+        row.out = d;
+        row.out_stride = stride;
+        row.perm = natural;
+        row.in_layout = LAYOUT_ROW;
+        row.out_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+        rc = run_pass(p, inv, col, L1, s);
+        if (!rc) rc = run_pass(p, inv, row, L2, s);
+    } else {
+        // rows first (the last forward stages, undone), then columns with the N^-1 scale
+        row.in = d;
+        row.in_stride = stride;
+        row.out = natural ? scr : d;
+        row.out_stride = natural ? N : stride;
+        row.perm = natural;
+        row.in_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+        row.out_layout = LAYOUT_ROW;
+        col.in = row.out;
+        col.in_stride = row.out_stride;
+        col.out = d;
+        col.out_stride = stride;
+        col.scale = 1;
+        rc = run_pass(p, inv, row, L2, s);
+        if (!rc) rc = run_pass(p, inv, col, L1, s);
+    }
+    if (scr) {
+        int rc2 = mq_pool_free(scr, s);
+        if (!rc) rc = rc2;
+    }
+    return rc;
+}
+
+extern "C" int ntt_forward(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
+    return ntt_run(p, d, batch, stride, stream, false);
+}
+
+extern "C" int ntt_inverse(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
+    return ntt_run(p, d, batch, stride, stream, true);
+}
+
+// ------------------------------------------------------------------------------------------------
+// BLAS
+// ------------------------------------------------------------------------------------------------
+
+static int blas(int op, void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width,
+                const uint64_t *scalar, void *stream) {
+    hm::u128 Q;
+    int rc = mq_check_modulus(q, width, &Q);
+    if (rc) return rc;
+    if (n == 0) return MQ_OK;
+    if ((rc = check_ptr(c, width, op == OP_AXPY ? "d_y" : "d_c")) || (rc = check_ptr(a, width, op == OP_AXPY ? "d_x" : "d_a")))
+        return rc;
+    if (op != OP_AXPY && (rc = check_ptr(b, width, "d_b"))) return rc;
+    if (n > SIZE_MAX / 16) return mq_fail(MQ_ERR_ARG, "n overflows");
+    BlasArgs args;
+    memset(&args, 0, sizeof args);
+    args.c = c;
+    args.a = a;
+    args.b = b;
+    args.n = n;
+    memcpy(args.q, q, sizeof args.q);
+    args.L = hm::bitlen(Q);
+    hm::to_words(hm::barrett_mu(Q, args.L), args.mu);
+    if (op == OP_AXPY) {
+        if (!scalar) return mq_fail(MQ_ERR_ARG, "scalar a is NULL");
+        hm::u128 s = hm::from_words(scalar);
+        if (width == MQ_W64 && scalar[1]) return mq_fail(MQ_ERR_RANGE, "scalar a must be < q");
+        if (s >= Q) return mq_fail(MQ_ERR_RANGE, "scalar a must be < q");
+        hm::to_words(s, args.s);
+        hm::to_words(hm::shoup(s, Q, width == MQ_W64 ? 64 : 128), args.sp);
+    }
+    cudaError_t e = launch_blas(width, op, args, (cudaStream_t)stream);
+    return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "BLAS launch");
+}
+
+extern "C" int mod_vadd(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    return blas(OP_VADD, c, a, b, n, q, width, nullptr, stream);
+}
+extern "C" int mod_vsub(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    return blas(OP_VSUB, c, a, b, n, q, width, nullptr, stream);
+}
+extern "C" int mod_vmul(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    return blas(OP_VMUL, c, a, b, n, q, width, nullptr, stream);
+}
+extern "C" int mod_axpy(void *y, const uint64_t a[2], const void *x, size_t n, const uint64_t q[2], int width,
+                        void *stream) {
+    // y = a*x + y: the kernel's first operand is x, the second (and the output) is y
+    return blas(OP_AXPY, y, x, y, n, q, width, a, stream);
+}

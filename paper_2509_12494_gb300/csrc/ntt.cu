@@ -1,0 +1,127 @@
+// ntt.cu -- twiddle-table construction and the dispatch of transform passes to the kernels
+// instantiated in ntt_w{64,128}_{fwd,inv}.cu (the kernels themselves are in ntt_kernel.cuh).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mq {
+
+cudaError_t launch_ntt_w1_fwd(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w1_inv(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w2_fwd(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w2_inv(int L, const PassArgs &a, cudaStream_t s);
+
+namespace {
+
+__device__ __forceinline__ unsigned brv(unsigned v, int bits) { return bits ? (__brev(v) >> (32 - bits)) : 0u; }
+
+// ------------------------------------------------------------------------------------------------
+// twiddle tables
+// ------------------------------------------------------------------------------------------------
+
+__device__ uint64_t shoup_companion(uint64_t w, uint64_t q) {  // floor(w * 2^64 / q), w < q < 2^63
+    uint64_t r = w, quo = 0;
+    for (int i = 0; i < 64; ++i) {
+        r <<= 1;
+        uint64_t bit = r >= q;
+        r -= bit ? q : 0;
+        quo = (quo << 1) | bit;
+    }
+    return quo;
+}
+
+__device__ uint4 shl1(uint4 v) {
+    return make_uint4(v.x << 1, (v.y << 1) | (v.x >> 31), (v.z << 1) | (v.y >> 31), (v.w << 1) | (v.z >> 31));
+}
+
+__device__ uint4 shoup_companion(uint4 w, uint4 q) {  // floor(w * 2^128 / q), w < q < 2^127
+    uint4 r = w, quo = make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < 128; ++i) {
+        r = shl1(r);
+        uint32_t m;
+        uint4 d = sub128(r, q, m);
+        r = sel128(m, r, d);
+        quo = shl1(quo);
+        quo.x |= (~m) & 1u;
+    }
+    return quo;
+}
+
+__device__ uint64_t pow_mod(uint64_t g, unsigned e, const Mod64 &m) {
+    uint64_t acc = 1 % m.q;
+    for (int b = 31; b >= 0; --b) {
+        acc = mul_mod_barrett(acc, acc, m);
+        if ((e >> b) & 1) acc = mul_mod_barrett(acc, g, m);
+    }
+    return acc;
+}
+
+__device__ uint4 pow_mod(uint4 g, unsigned e, const Mod128 &m) {
+    uint4 acc = make_uint4(1, 0, 0, 0);
+    for (int b = 31; b >= 0; --b) {
+        acc = mul_mod_barrett(acc, acc, m);
+        if ((e >> b) & 1) acc = mul_mod_barrett(acc, g, m);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ unsigned table_exponent(unsigned k, int logN, int cyclic) {
+    if (k == 0) return 0;
+    if (!cyclic) return brv(k, logN);
+    unsigned m = 1u << (31 - __clz(k));
+    return brv(k - m, logN - 1);
+}
+
+__global__ void twiddle_kernel64(int logN, int cyclic, Mod64 m, uint64_t root, uint64_t root_inv, Tw64 *fwd, Tw64 *inv) {
+    unsigned N = 1u << logN;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        unsigned e = table_exponent(k, logN, cyclic);
+        uint64_t w = pow_mod(root, e, m), wi = pow_mod(root_inv, e, m);
+        fwd[k] = Tw64{w, shoup_companion(w, m.q)};
+        inv[k] = Tw64{wi, shoup_companion(wi, m.q)};
+    }
+}
+
+__global__ void twiddle_kernel128(int logN, int cyclic, Mod128 m, uint4 root, uint4 root_inv, Tw128 *fwd, Tw128 *inv) {
+    unsigned N = 1u << logN;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        unsigned e = table_exponent(k, logN, cyclic);
+        uint4 w = pow_mod(root, e, m), wi = pow_mod(root_inv, e, m);
+        Tw128 f, v;
+        f.w = w;
+        f.wp = shoup_companion(w, m.q);
+        v.w = wi;
+        v.wp = shoup_companion(wi, m.q);
+        fwd[k] = f;
+        inv[k] = v;
+    }
+}
+
+uint4 to_u4(const uint64_t v[2]) {
+    return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
+}
+
+}  // namespace
+
+cudaError_t launch_ntt_pass(int width, int L, bool inv, const PassArgs &a, cudaStream_t s) {
+    if (width == 1) return inv ? launch_ntt_w1_inv(L, a, s) : launch_ntt_w1_fwd(L, a, s);
+    return inv ? launch_ntt_w2_inv(L, a, s) : launch_ntt_w2_fwd(L, a, s);
+}
+
+cudaError_t launch_twiddle_build(int width, int logN, int cyclic, const uint64_t q[2], const uint64_t root[2],
+                                 const uint64_t root_inv[2], const uint64_t mu[2], int L, void *tw_fwd,
+                                 void *tw_inv, cudaStream_t s) {
+    unsigned N = 1u << logN;
+    unsigned threads = 256, blocks = (N + threads - 1) / threads;
+    if (width == 1) {
+        Mod64 m{q[0], mu[0], L};
+        twiddle_kernel64<<<blocks, threads, 0, s>>>(logN, cyclic, m, root[0], root_inv[0], (Tw64 *)tw_fwd, (Tw64 *)tw_inv);
+    } else {
+        Mod128 m{to_u4(q), to_u4(mu), L};
+        twiddle_kernel128<<<blocks, threads, 0, s>>>(logN, cyclic, m, to_u4(root), to_u4(root_inv), (Tw128 *)tw_fwd,
+                                                     (Tw128 *)tw_inv);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mq

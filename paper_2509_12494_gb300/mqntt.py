@@ -1,0 +1,197 @@
+"""Thin Python binding of the C ABI in include/mqntt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but convert
+arguments: Python ints become two-word arrays, torch tensors become device pointers, a torch
+stream (or None for the current stream) becomes a cudaStream_t.  All arithmetic runs in the CUDA
+library ``libmqntt.so``; there is no fallback.  A non-zero status raises ``MqError`` carrying the
+library's message.
+
+Residue tensors are int64 tensors on the GPU holding the residues' bits: shape (..., ) for 64-bit
+residues and (..., 2) -- low word first -- for 128-bit residues.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+MQ_OK = 0
+MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_ALIGN = -1, -2, -3, -4, -5
+MQ_ERR_OOM, MQ_ERR_CUDA, MQ_ERR_TIMEOUT, MQ_ERR_RANGE, MQ_ERR_STATE = -6, -7, -8, -9, -10
+MQ_W64, MQ_W128 = 1, 2
+MQ_NEGACYCLIC, MQ_CYCLIC, MQ_ORDER_NATURAL, MQ_ORDER_BITREV = 0, 1, 0, 2
+
+_u64x2 = ctypes.c_uint64 * 2
+_vp = ctypes.c_void_p
+_lib = None
+
+
+class MqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mqntt error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmqntt.so (compiled by __graft_entry__.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c "
+                               "'import __graft_entry__ as g; g.build()')")
+        _build.build()
+    L = ctypes.CDLL(path)
+    sig = {
+        "ntt_plan_create": [ctypes.POINTER(_vp), ctypes.c_uint, _u64x2, _u64x2, ctypes.c_int, ctypes.c_uint, _vp],
+        "ntt_plan_destroy": [_vp],
+        "ntt_forward": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
+        "ntt_inverse": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
+        "ntt_plan_info": [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint)],
+        "mod_vadd": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
+        "mod_vsub": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
+        "mod_vmul": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
+        "mod_axpy": [_vp, _u64x2, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
+        "mq_probe_imad_rate": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), _vp],
+        "mq_last_error": [],
+        "mq_version": [],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name in ("mq_last_error", "mq_version") else ctypes.c_int
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------------------- helpers
+
+def words(v: int) -> "ctypes.Array":
+    v = int(v)
+    if v < 0 or v >= 2**128:
+        raise ValueError("value must be in [0, 2^128)")
+    return _u64x2(v & (2**64 - 1), v >> 64)
+
+
+def ptr(x) -> int:
+    """Device pointer of a torch tensor, or an int passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_handle(stream=None) -> int:
+    """cudaStream_t of a torch stream; None means torch's current stream."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(rc: int):
+    if rc != MQ_OK:
+        raise MqError(rc, (load().mq_last_error() or b"").decode())
+
+
+def width_of(q: int) -> int:
+    return MQ_W64 if q < 2**60 else MQ_W128
+
+
+# ---------------------------------------------------------------------------------------- the ABI
+
+class Plan:
+    """Owns an ntt_plan* (freed by ntt_plan_destroy or on garbage collection)."""
+
+    def __init__(self, handle: int, log2n: int, width: int, flags: int):
+        self.handle, self.log2n, self.width, self.flags = handle, log2n, width, flags
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ntt_plan_destroy(self.handle)
+            self.handle = None
+
+
+def ntt_plan_create(log2n: int, q: int, root: int, width: int, flags: int = 0, stream=None) -> Plan:
+    h = _vp()
+    _check(load().ntt_plan_create(ctypes.byref(h), log2n, words(q), words(root), width, flags, stream_handle(stream)))
+    return Plan(h.value, log2n, width, flags)
+
+
+def ntt_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(load().ntt_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def ntt_forward(plan: Plan, data, batch: int = 1, stride: int = 0, stream=None):
+    _check(load().ntt_forward(plan.handle, ptr(data), batch, stride, stream_handle(stream)))
+
+
+def ntt_inverse(plan: Plan, data, batch: int = 1, stride: int = 0, stream=None):
+    _check(load().ntt_inverse(plan.handle, ptr(data), batch, stride, stream_handle(stream)))
+
+
+def ntt_plan_info(plan: Plan):
+    a, b, c = ctypes.c_uint(), ctypes.c_int(), ctypes.c_uint()
+    _check(load().ntt_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def mod_vadd(c, a, b, n: int, q: int, width: int, stream=None):
+    _check(load().mod_vadd(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+
+
+def mod_vsub(c, a, b, n: int, q: int, width: int, stream=None):
+    _check(load().mod_vsub(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+
+
+def mod_vmul(c, a, b, n: int, q: int, width: int, stream=None):
+    _check(load().mod_vmul(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+
+
+def mod_axpy(y, a: int, x, n: int, q: int, width: int, stream=None):
+    _check(load().mod_axpy(ptr(y), words(a), ptr(x), n, words(q), width, stream_handle(stream)))
+
+
+MQ_PROBE_MAD_LO, MQ_PROBE_MAD_HI, MQ_PROBE_MAD_CC = 0, 1, 2
+
+
+def mq_probe_imad_rate(kind: int, iters: int, stream=None):
+    """(thread-instructions per second, kernel ms) of the multiply-add probe."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().mq_probe_imad_rate(kind, iters, ctypes.byref(r), ctypes.byref(ms), stream_handle(stream)))
+    return r.value, ms.value
+
+
+def mq_last_error() -> str:
+    return (load().mq_last_error() or b"").decode()
+
+
+def mq_version() -> str:
+    return load().mq_version().decode()
+
+
+# ------------------------------------------------------------------------- tensor marshalling
+
+def to_device(a: np.ndarray, device="cuda"):
+    """numpy uint64 residues -> int64 torch tensor with the same bits on the GPU."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def to_host(t) -> np.ndarray:
+    """GPU int64 tensor -> numpy uint64 with the same bits."""
+    return t.detach().cpu().numpy().view(np.uint64)

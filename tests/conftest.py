@@ -25,3 +25,23 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def mq():
+    """The CUDA library, built if needed; GPU tests only."""
+    import torch
+    from paper_2509_12494_gb300 import _build
+    from paper_2509_12494_gb300 import mqntt as M
+    _build.build()
+    M.load()
+    torch.cuda.set_device(0)
+    return M
+
+
+@pytest.fixture(scope="session")
+def pool():
+    """Thread pool for oracle calls (ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(2, os.cpu_count() or 2)) as ex:
+        yield ex

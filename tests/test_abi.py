@@ -1,0 +1,93 @@
+"""The C ABI library loads without a GPU, exports every declared symbol, and rejects bad arguments
+before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2509_12494_gb300 import _build
+from paper_2509_12494_gb300 import mqntt as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof"):
+                names.add(name)
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return M.load()
+
+
+def test_header_declares_the_core_abi():
+    names = declared_functions()
+    for n in ("ntt_plan_create", "ntt_plan_destroy", "ntt_forward", "ntt_inverse", "mod_vadd", "mod_vsub", "mod_vmul",
+              "mod_axpy", "mq_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(_build.LIB)
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version(lib):
+    assert "mqntt" in M.mq_version()
+
+
+Q124 = (1 << 123) + (1 << 20) + 1   # not checked for primality: the checks below fail earlier
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(log2n=0), M.MQ_ERR_SIZE),
+    (dict(log2n=25), M.MQ_ERR_SIZE),
+    (dict(q=2**124 + 1), M.MQ_ERR_MODULUS),
+    (dict(q=2**60 + 1, width=M.MQ_W64), M.MQ_ERR_MODULUS),
+    (dict(q=(1 << 100)), M.MQ_ERR_MODULUS),            # even
+    (dict(q=(3 << 100) + 3), M.MQ_ERR_MODULUS),         # q - 1 not divisible by 2N
+    (dict(width=3), M.MQ_ERR_ARG),
+    (dict(flags=8), M.MQ_ERR_ARG),
+    (dict(root=0), M.MQ_ERR_ROOT),
+    (dict(root=Q124), M.MQ_ERR_ROOT),                   # root >= q
+    (dict(root=1), M.MQ_ERR_ROOT),                      # wrong order
+])
+def test_plan_create_rejects(lib, kw, code):
+    args = dict(log2n=10, q=Q124, root=5, width=M.MQ_W128, flags=0)
+    args.update(kw)
+    with pytest.raises(M.MqError) as e:
+        M.ntt_plan_create(args["log2n"], args["q"], args["root"], args["width"], args["flags"], stream=0)
+    assert e.value.code == code, M.mq_last_error()
+    assert M.mq_last_error()
+
+
+@pytest.mark.parametrize("fn", ["mod_vadd", "mod_vsub", "mod_vmul"])
+def test_blas_rejects(lib, fn):
+    f = getattr(M, fn)
+    with pytest.raises(M.MqError) as e:   # even modulus
+        f(16, 16, 16, 4, 2**61, M.MQ_W128, stream=0)
+    assert e.value.code == M.MQ_ERR_MODULUS
+    with pytest.raises(M.MqError) as e:   # misaligned pointer for 128-bit residues
+        f(24, 16, 16, 4, Q124, M.MQ_W128, stream=0)
+    assert e.value.code == M.MQ_ERR_ALIGN
+    with pytest.raises(M.MqError) as e:
+        f(None, 16, 16, 4, Q124, M.MQ_W128, stream=0)
+    assert e.value.code == M.MQ_ERR_ARG
+    f(None, None, None, 0, Q124, M.MQ_W128, stream=0)  # n == 0 is a no-op, pointers unused
+
+
+def test_axpy_scalar_range(lib):
+    with pytest.raises(M.MqError) as e:
+        M.mod_axpy(16, Q124, 16, 4, Q124, M.MQ_W128, stream=0)
+    assert e.value.code == M.MQ_ERR_RANGE

@@ -1,0 +1,129 @@
+"""GPU transforms vs the CPU oracle, element by element (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_12494_gb300 import workload as W
+from tests.gpu_util import sample_idx
+
+pytestmark = pytest.mark.gpu
+
+Q60 = W.gen_prime(60, 18, 301)
+Q124 = W.gen_prime(124, 18, 302)
+FLAGS = {"nega_nat": 0, "nega_brv": 2, "cyc_nat": 1, "cyc_brv": 3}
+
+
+def _ofl(flags):  # library flags -> oracle flags (same bit meaning, defined independently)
+    return (oracle.CYCLIC if flags & 1 else 0) | (oracle.BITREV if flags & 2 else 0)
+
+
+def _gpu_transform(M, plan, x, batch, stride, inverse):
+    import torch
+    d = M.to_device(x)
+    (M.ntt_inverse if inverse else M.ntt_forward)(plan, d, batch, stride)
+    torch.cuda.synchronize()
+    return M.to_host(d)
+
+
+def _strided(x_flat, batch, stride, N, width):
+    shp = (batch, stride) if width == 1 else (batch, stride, 2)
+    return x_flat.reshape(shp)
+
+
+@pytest.mark.parametrize("flag", list(FLAGS))
+@pytest.mark.parametrize("width", [1, 2])
+@pytest.mark.parametrize("log2n", list(range(1, 15)))
+def test_ntt_vs_oracle(mq, pool, log2n, width, flag):
+    """Every size from 2 to 2^14 (one-pass and two-pass kernels), both directions, a batch with a
+    stride longer than N whose gaps must stay untouched."""
+    if log2n >= 13 and flag.startswith("cyc"):
+        pytest.skip("cyclic checked up to 2^12 here and at 2^16 in the sampled test")
+    q = Q60 if width == 1 else Q124
+    flags = FLAGS[flag]
+    cyclic = bool(flags & 1)
+    root = W.gen_root(q, log2n, seed=log2n, cyclic=cyclic)
+    N = 1 << log2n
+    batch = 3 if log2n <= 10 else (2 if log2n <= 12 else 1)
+    stride = N + 3
+    flat = W.gen_residues(batch * stride, q, seed=log2n * 7 + width, width=width)
+    plan = mq.ntt_plan_create(log2n, q, root, width, flags)
+    fut = [pool.submit(oracle.ntt, _strided(flat, batch, stride, N, width)[b, :N].copy(), log2n, q, root, width,
+                       _ofl(flags)) for b in range(batch)]
+    got = _strided(_gpu_transform(mq, plan, flat, batch, stride, False), batch, stride, N, width)
+    for b in range(batch):
+        assert np.array_equal(got[b, :N], fut[b].result()), f"forward, polynomial {b}"
+        assert np.array_equal(got[b, N:], _strided(flat, batch, stride, N, width)[b, N:]), "gap written"
+    # inverse on independent random spectra, and the round trip
+    fut = [pool.submit(oracle.ntt, _strided(flat, batch, stride, N, width)[b, :N].copy(), log2n, q, root, width,
+                       _ofl(flags), True) for b in range(batch)]
+    got_i = _strided(_gpu_transform(mq, plan, flat, batch, stride, True), batch, stride, N, width)
+    for b in range(batch):
+        assert np.array_equal(got_i[b, :N], fut[b].result()), f"inverse, polynomial {b}"
+    back = _strided(_gpu_transform(mq, plan, got.reshape(flat.shape).copy(), batch, stride, True), batch, stride, N,
+                    width)
+    assert np.array_equal(back, _strided(flat, batch, stride, N, width))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_single_1024_124bit(mq, seed):
+    """One negacyclic forward + inverse, N = 1024, seeded 124-bit q = 1 mod 2048, all outputs."""
+    q = W.gen_prime(124, 11, seed)
+    psi = W.gen_root(q, 10, seed)
+    x = W.gen_residues(1024, q, seed, width=2)
+    plan = mq.ntt_plan_create(10, q, psi, 2)
+    y = _gpu_transform(mq, plan, x, 1, 1024, False)
+    assert np.array_equal(y, oracle.ntt(x, 10, q, psi, 2))
+    assert np.array_equal(_gpu_transform(mq, plan, y, 1, 1024, True), x)
+
+
+@pytest.mark.parametrize("flag", ["nega_nat", "nega_brv", "cyc_nat"])
+@pytest.mark.parametrize("width", [1, 2])
+@pytest.mark.parametrize("log2n", [16, 17])
+def test_ntt_full_size_sampled(mq, pool, log2n, width, flag):
+    """Full FHE sizes: sampled outputs from the definition, and the exact round trip."""
+    q = Q60 if width == 1 else Q124
+    flags = FLAGS[flag]
+    cyclic = bool(flags & 1)
+    root = W.gen_root(q, log2n, seed=9, cyclic=cyclic)
+    N, batch = 1 << log2n, 2
+    x = W.gen_residues(batch * N, q, seed=log2n + width, width=width)
+    plan = mq.ntt_plan_create(log2n, q, root, width, flags)
+    y = _gpu_transform(mq, plan, x, batch, N, False)
+    xs, ys = _strided(x, batch, N, N, width), _strided(y, batch, N, N, width)
+    bits = log2n
+    checks = []
+    for b in range(batch):
+        for i in sample_idx(N, 6, seed=b + log2n):
+            k = int(i) if not flags & 2 else int(format(int(i), f"0{bits}b")[::-1], 2)
+            checks.append((b, int(i), pool.submit(oracle.ntt_point, xs[b], log2n, q, root, width, k, _ofl(flags) & 1)))
+    for b, i, f in checks:
+        assert W.to_ints(ys[b][i:i + 1])[0] == f.result(), (b, i)
+    assert np.array_equal(_gpu_transform(mq, plan, y, batch, N, True), x)
+
+
+def test_uniform_batch_256x65536(mq, pool):
+    """The uniform batched workload (256 transforms of 2^16, 124-bit q): sampled outputs of the
+    forward transform and the exact round trip, in the launch configuration the benchmark times."""
+    import torch
+    log2n, batch = 16, 256
+    q = W.gen_prime(124, 17, 1)
+    psi = W.gen_root(q, log2n, 1)
+    N = 1 << log2n
+    x = W.gen_residues(batch * N, q, seed=11, width=2)
+    for flags in (2, 0):
+        plan = mq.ntt_plan_create(log2n, q, psi, 2, flags)
+        d = mq.to_device(x)
+        mq.ntt_forward(plan, d, batch, N)
+        torch.cuda.synchronize()
+        y = mq.to_host(d).reshape(batch, N, 2)
+        xs = x.reshape(batch, N, 2)
+        checks = []
+        for b in (0, 77, 255):
+            for i in sample_idx(N, 3, seed=b):
+                k = int(i) if not flags & 2 else int(format(int(i), "016b")[::-1], 2)
+                checks.append((b, int(i), pool.submit(oracle.ntt_point, xs[b], log2n, q, psi, 2, k)))
+        for b, i, f in checks:
+            assert W.to_ints(y[b][i:i + 1])[0] == f.result(), (flags, b, i)
+        mq.ntt_inverse(plan, d, batch, N)
+        torch.cuda.synchronize()
+        assert np.array_equal(mq.to_host(d), x)
