@@ -96,6 +96,25 @@ int ntt_forward(const ntt_plan *plan, void *d_data, size_t batch, size_t stride,
  */
 int ntt_inverse(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
 
+/*
+ * ntt_forward without any device allocation (the paper has no counterpart: this is a deployment
+ * variant).  For callers that cannot allocate device memory while running -- a service that
+ * reserves its memory budget at start-up, code sharing the GPU with a framework whose allocator
+ * owns the free memory, code recorded into a graph that must not contain allocation nodes.
+ * Same arguments and results as ntt_forward.  Natural-order transforms with N > 2^12 stage through
+ * a static device buffer of MQ_NOALLOC_SCRATCH_BYTES that the library holds on every device that
+ * loads it, until the process exits; a call needing more (batch * N * 8 * width bytes) fails with
+ * MQ_ERR_SIZE -- split the batch.  Other transforms need no staging and take any batch.
+ * The buffer is shared by all calls: calls that overlap on the GPU (different streams, or
+ * different host threads without ordering) race on it and give wrong results.  The first call on
+ * each device looks up the buffer's device address (cudaGetSymbolAddress, which may load the
+ * library's device code); make that first call before any stream capture.
+ * Errors: those of ntt_forward, except MQ_ERR_OOM; MQ_ERR_SIZE for an oversized batch;
+ * MQ_ERR_ARG if the plan belongs to another device than the current one.
+ */
+#define MQ_NOALLOC_SCRATCH_BYTES (16u << 20) /* 16 MiB */
+int ntt_forward_noalloc(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
+
 /* Plan properties (for callers that size buffers from a plan). */
 int ntt_plan_info(const ntt_plan *plan, unsigned *log2n, int *width, unsigned *flags);
 

@@ -13,6 +13,7 @@
 #include "../../include/mqntt.h"
 #include "common.cuh"
 #include "hostmath.h"
+#include "plan.h"
 
 using namespace mq;
 
@@ -103,19 +104,6 @@ int mq_pool_free(void *p, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------------
 // plans
 // ------------------------------------------------------------------------------------------------
-
-struct ntt_plan {
-    int device;
-    unsigned log2n;
-    int width;
-    unsigned flags;
-    uint64_t q[2], mu[2];
-    int L;  // bit length of q
-    uint64_t root[2], root_inv[2];
-    void *tw_fwd, *tw_inv;  // N entries of (w, w') each
-    uint64_t sc[2], scp[2], ws[2], wsp[2];
-    int L1;  // rows of the N1 x N2 split (0: single pass)
-};
 
 static int split_of(unsigned log2n) { return log2n <= 12 ? 0 : (int)(log2n / 2); }
 
