@@ -3,8 +3,10 @@
 
 Default workload (one "step"): 256 independent negacyclic NTTs of N = 2^16 under a seeded 124-bit
 prime q = 1 mod 2^17, forward then inverse, in place in HBM, through the C ABI.  The timed `value`
-is the batched form; the plain per-call form (one ntt_forward / ntt_inverse call per polynomial)
-is timed beside it.  BLAS (vadd, vsub, vmul, axpy at n = 2^24, 60- and 124-bit) is reported as an
+is the batched persistent form (mqntt_batch.h: 256 forward jobs and 256 inverse jobs, each inverse
+waiting for its forward, one persistent kernel replayed from a CUDA graph); beside it are the
+same work as one ntt_forward + one ntt_inverse call over the whole batch ("batched_call") and as
+one call per polynomial ("plain").  BLAS (vadd, vsub, vmul, axpy at n = 2^24, 60- and 124-bit) is reported as an
 extra block.  One JSON line on stdout (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mq|reference] [--bits 124|60]
@@ -152,9 +154,18 @@ def run_gpu(args, rank, world):
     flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
 
-    def step_batched():
+    def step_call():
         M.ntt_forward(plan, d, batch, N, stream=sh)
         M.ntt_inverse(plan, d, batch, N, stream=sh)
+
+    # the persistent batch: job i = forward of polynomial i, job batch + i = its inverse
+    jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
+    jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
+    pbatch = M.mq_batch_create(jobs, stream=sh)
+    pinfo = M.mq_batch_info(pbatch)
+
+    def step_batched():
+        M.mq_batch_launch(pbatch, stream=sh)
 
     row = width if width == 2 else 1
 
@@ -215,23 +226,33 @@ def run_gpu(args, rank, world):
     value = bfly * world / (ms * 1e-3)
 
     # correctness of what was timed: the round trip leaves the input unchanged
-    ok_roundtrip = bool(np.array_equal(M.to_host(d), x_host))
+    batch_status = M.mq_batch_status(pbatch)
+    ok_roundtrip = bool(np.array_equal(M.to_host(d), x_host)) and batch_status == 0
 
     out = {"metric": METRIC, "value": value, "unit": "butterflies/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u128" if width == 2 else "u64", "data": "synthetic",
            "config": {"workload": workload_name(wl, args), "batch": batch, "log2n": wl["log2n"],
-                      "q_bits": args.bits, "order": args.order, "form": "batched (one call per direction)",
+                      "q_bits": args.bits, "order": args.order,
+                      "form": f"batched persistent kernel in a CUDA graph ({pinfo['items']} work items, "
+                              f"{pinfo['ctas']} CTAs)",
                       "l2": "L2 flushed between timed steps (2 x L2 write); working set "
                             f"{batch * N * 8 * width >> 20} MiB", "parallelism": f"replicas x{world}"},
            "roundtrip_bit_exact": ok_roundtrip}
 
-    # gpu launches in the timed region: two passes per direction for N > 2^12, one otherwise
+    # gpu launches in the timed region: one persistent kernel per step (plus a counter memset and
+    # a 4-byte status copy in the same graph)
     passes = 1 if wl["log2n"] <= 12 else 2
-    out["gpu_launches"] = args.steps * 2 * passes
+    out["gpu_launches"] = args.steps
 
     if rank != 0:
         return None
+
+    # the same work as one call per direction over the whole batch
+    t_call = timed(step_call, max(3, args.steps), 1)
+    ms_call = sum(t_call) / len(t_call)
+    out["batched_call"] = {"value": bfly / (ms_call * 1e-3), "unit": "butterflies/s", "ms_per_step": ms_call,
+                           "form": f"ntt_forward + ntt_inverse over all {batch} polynomials ({2 * passes} launches)"}
 
     # plain per-call path
     if not args.no_plain:
@@ -241,40 +262,43 @@ def run_gpu(args, rank, world):
                         "form": f"{batch} ntt_forward + {batch} ntt_inverse calls of batch 1",
                         "batched_over_plain": ms_plain / ms}
 
-    # roofline of the transform kernels
+    # roofline of the dominant kernel: the persistent kernel, one launch per step (event-timed
+    # median of single-launch steps); the per-pass kernels of the one-call form beside it
+    t_roof = timed(step_batched, max(5, args.steps), 1)
+    ms_launch = statistics.median(t_roof)
     fw, iv = timed_dirs(max(3, args.steps))
     ms_f, ms_i = statistics.median(fw), statistics.median(iv)
     mads_per_mul = 64 if width == 2 else 16   # 32-bit multiply instructions per Shoup product
     mad_f = wl["butterflies_per_dir"] * mads_per_mul
     mad_i = (wl["butterflies_per_dir"] + batch * N // 2) * mads_per_mul  # + N/2 folded N^-1 products
-    per_launch_ms = (ms_f + ms_i) / (2 * passes)
-    alu_achieved = (mad_f + mad_i) / ((ms_f + ms_i) * 1e-3)
+    alu_achieved = (mad_f + mad_i) / (ms_launch * 1e-3)
     probe = {}
     for kind, name in ((M.MQ_PROBE_MAD_CC, "mad_cc"), (M.MQ_PROBE_MAD_LO, "mad_lo"), (M.MQ_PROBE_MAD_HI, "mad_hi")):
         rate, pms = M.mq_probe_imad_rate(kind, 4000, stream=sh)
         probe[name] = rate
     alu_peak = probe["mad_cc"]
-    bytes_per_launch = 2 * batch * N * 8 * width   # each pass reads and writes every residue once
+    bytes_per_launch = 2 * passes * 2 * batch * N * 8 * width   # every pass reads and writes each residue
     hbm_peak = measured_peaks().get("hbm_gbs")
     hbm_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or HBM_FALLBACK_GBS
-    hbm_achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    hbm_achieved = bytes_per_launch / (ms_launch * 1e-3) / 1e9
     alu_frac, hbm_frac = alu_achieved / alu_peak, hbm_achieved / hbm_peak
     if alu_frac >= hbm_frac:
         out["roofline"] = {"bound": "alu", "achieved": alu_achieved / 1e12, "peak": alu_peak / 1e12,
                            "unit": "T mad32/s", "frac": alu_frac, "traffic": None,
-                           "kernel": "ntt_pass_kernel (all passes of one step)",
+                           "kernel": "persistent_kernel (one launch = one step)",
                            "peak_source": "measured by mq_probe_imad_rate (carry-chained mad.lo.cc/madc.hi.cc)",
                            "algorithmic": f"{mads_per_mul} 32-bit multiply instructions per Shoup product",
                            "hbm_frac": hbm_frac, "hbm_achieved_gbs": hbm_achieved,
-                           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
+                           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src, "ms_launch": ms_launch}
     else:
         out["roofline"] = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                           "frac": hbm_frac, "traffic": None, "kernel": "ntt_pass_kernel",
-                           "peak_source": hbm_src, "alu_frac": alu_frac,
+                           "frac": hbm_frac, "traffic": None, "kernel": "persistent_kernel (one launch = one step)",
+                           "peak_source": hbm_src, "alu_frac": alu_frac, "ms_launch": ms_launch,
                            "alu_achieved_tmads": alu_achieved / 1e12, "alu_peak_tmads": alu_peak / 1e12}
-    out["roofline"]["ms_forward"] = ms_f
-    out["roofline"]["ms_inverse"] = ms_i
+    out["roofline"]["call_form_alu_frac"] = (mad_f + mad_i) / ((ms_f + ms_i) * 1e-3) / alu_peak
+    out["roofline"]["call_form_ms_forward"] = ms_f
+    out["roofline"]["call_form_ms_inverse"] = ms_i
     out["probe_mad_per_s"] = probe
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region

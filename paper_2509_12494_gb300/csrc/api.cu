@@ -227,6 +227,7 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
         a.in_layout = (inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
         a.out_layout = (!inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
         a.scale = inv;
+        a.final = 1;
         return run_pass(p, inv, a, logN, s);
     }
 
@@ -252,6 +253,7 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
         row.perm = natural;
         row.in_layout = LAYOUT_ROW;
         row.out_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+        row.final = 1;
         rc = run_pass(p, inv, col, L1, s);
         if (!rc) rc = run_pass(p, inv, row, L2, s);
     } else {
@@ -268,6 +270,7 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
         col.out = d;
         col.out_stride = stride;
         col.scale = 1;
+        col.final = 1;
         rc = run_pass(p, inv, row, L2, s);
         if (!rc) rc = run_pass(p, inv, col, L1, s);
     }

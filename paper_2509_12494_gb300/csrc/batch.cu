@@ -1,0 +1,953 @@
+// batch.cu -- the batched persistent form (include/mqntt_batch.h).
+//
+// A batch is a list of jobs (NTT passes of plans, BLAS operations) expanded on the host into work
+// items of one CTA each: a group of transform tiles (the same tile_group code as the per-call
+// kernels) or a chunk of a BLAS vector.  One persistent kernel, one wave of CTAs, takes items in
+// order from a device counter.  Dependencies always point to earlier items:
+//   * the second pass of a two-pass transform waits for the first pass of the same polynomial
+//     (a per-polynomial counter of finished first-pass items);
+//   * the first items of a job with `after` wait for every item of that job (a per-job counter).
+// Items are ordered by a software-pipelining key: job chains (a job and the jobs that depend on
+// it) are numbered in submission order, and an item of stage s (its pass, plus the stages of the
+// jobs before it in its chain) of chain c gets the key c + s * lag, so a dependent stage trails
+// its producer by `lag` chains and its waits are normally already satisfied.
+// Deadlock freedom: an item waits only for items fetched before it; those were fetched by CTAs
+// that are running, whose own waits are again for earlier items, so every wait ends.  Each wait
+// is still bounded (globaltimer) and sets the batch status to MQ_ERR_TIMEOUT when it gives up;
+// every CTA then drains out, so a broken batch never hangs the GPU.
+// Memory ordering: a finished item's threads fence, the CTA synchronises, and one thread adds to
+// the counters; a waiting thread reads counters with ld.acquire.gpu and the CTA synchronises
+// before touching data.  Data moves through L2 (.cg loads and stores), so no SM reads a stale L1
+// line of a buffer another SM rewrote during the launch.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mqntt_batch.h"
+#include "blas_ops.cuh"
+#include "common.cuh"
+#include "hostmath.h"
+#include "ntt_kernel.cuh"
+#include "plan.h"
+
+int mq_fail(int code, const char *fmt, ...);
+int mq_cuda_fail(cudaError_t e, const char *where);
+int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv);
+
+namespace mq {
+namespace batch_detail {
+
+using ntt_detail::Shape;
+using ntt_detail::Traits;
+
+constexpr int BT = 256;               // threads per persistent CTA
+constexpr int LMIN = 6, LMAX = 11;    // tile sizes the persistent kernel carries
+constexpr int JK_NTT = 0, JK_BLAS = 1;
+
+struct JobDev {
+    int kind;        // JK_NTT or JK_BLAS
+    int width;       // 1 or 2 words per residue
+    int inv;         // NTT direction
+    int op;          // BLAS op (OP_*)
+    int after;       // job this one waits for, or -1
+    int twopass;     // NTT: two passes (per-polynomial counters)
+    int L[2];        // NTT: tile log size of pass 0 and pass 1
+    unsigned n_items;     // items of this job (target of its completion counter)
+    unsigned poly_base;   // two-pass NTT: index of polynomial 0's counter
+    unsigned groups0;     // two-pass NTT: pass-0 items per polynomial
+    unsigned pad;
+    unsigned long long chunk;  // BLAS: residues per item
+    PassArgs pa[2];            // NTT passes
+    BlasArgs ba;               // BLAS operands
+};
+
+struct ItemDev {
+    unsigned job;
+    unsigned pass;
+    unsigned poly;
+    unsigned pad;
+    unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_status(const unsigned *p) {
+    return (int)*(const volatile unsigned *)p;
+}
+
+// Bounded wait until *ctr >= target.  Returns false on timeout or when the batch already failed.
+__device__ bool wait_geq(const unsigned *ctr, unsigned target, const unsigned *status, unsigned long long limit_ns) {
+    if (ld_acquire(ctr) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        __nanosleep(200);
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_status(status) != 0) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ uint4 u4(const uint64_t v[2]) {
+    return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
+}
+
+// residues [begin, end) of a BLAS job; 16-byte aligned operands (checked on the host)
+template <int W, int OP>
+__device__ __forceinline__ void blas_chunk(const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
+    if (W == 2) {
+        const Mod128 m{u4(b.q), u4(b.mu), b.L};
+        const uint4 s = u4(b.s), sp = u4(b.sp);
+        const uint4 *A = reinterpret_cast<const uint4 *>(b.a), *B = reinterpret_cast<const uint4 *>(b.b);
+        uint4 *C = reinterpret_cast<uint4 *>(b.c);
+        // one residue per thread and step: the wave of resident CTAs keeps enough loads in flight,
+        // and an unrolled Barrett would spill inside this many-branched kernel
+        for (unsigned long long i = begin + tid; i < end; i += BT) {
+            const uint4 va = __ldcg(A + i), vb = __ldcg(B + i);
+            __stcg(C + i, op128<OP>(va, vb, m, s, sp));
+        }
+    } else {
+        const Mod64 m{b.q[0], b.mu[0], b.L};
+        const uint64_t s = b.s[0], sp = b.sp[0];
+        // begin is a multiple of the (even) chunk: pairs first, then a possible odd last residue
+        const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(b.a), *B = reinterpret_cast<const ulonglong2 *>(b.b);
+        ulonglong2 *C = reinterpret_cast<ulonglong2 *>(b.c);
+        const unsigned long long vb0 = begin / 2, ve = end / 2;
+        for (unsigned long long i = vb0 + tid; i < ve; i += BT) {
+            ulonglong2 x = __ldcg(A + i), y = __ldcg(B + i), r;
+            r.x = op64<OP>(x.x, y.x, m, s, sp);
+            r.y = op64<OP>(x.y, y.y, m, s, sp);
+            __stcg(C + i, r);
+        }
+        if ((end & 1) && tid == 0) {
+            const unsigned long long *a1 = reinterpret_cast<const unsigned long long *>(b.a);
+            const unsigned long long *b1 = reinterpret_cast<const unsigned long long *>(b.b);
+            unsigned long long *c1 = reinterpret_cast<unsigned long long *>(b.c);
+            c1[end - 1] = op64<OP>(__ldcg(a1 + end - 1), __ldcg(b1 + end - 1), m, s, sp);
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void run_blas(int op, const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
+    switch (op) {
+    case OP_VADD: blas_chunk<W, OP_VADD>(b, begin, end, tid); break;
+    case OP_VSUB: blas_chunk<W, OP_VSUB>(b, begin, end, tid); break;
+    case OP_VMUL: blas_chunk<W, OP_VMUL>(b, begin, end, tid); break;
+    default: blas_chunk<W, OP_AXPY>(b, begin, end, tid); break;
+    }
+}
+
+constexpr int PT = 32;              // producer threads (one warp)
+constexpr int CT = BT + PT;         // threads per persistent CTA
+constexpr int BAR_COMPUTE = 1;      // named barrier of the BT compute threads
+constexpr int BAR_FULL = 2;         // + buffer: producer -> compute, "buffer b holds item k"
+constexpr int BAR_EMPTY = 4;        // + buffer: compute -> producer, "buffer b is free again"
+
+// named barriers with immediate ids (a register id would make ptxas reserve all sixteen)
+__device__ __forceinline__ void bar_arrive(int id) {
+    if (id == BAR_FULL) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
+    else if (id == BAR_FULL + 1) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
+    else if (id == BAR_EMPTY) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
+    else asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id) {
+    if (id == BAR_FULL) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
+    else if (id == BAR_FULL + 1) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
+    else if (id == BAR_EMPTY) asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
+}
+
+// Stage an item's tiles with the producer warp: cp.async through L2 for 128-bit residues, batched
+// L2 loads for 64-bit residues (an 8-byte cp.async would allocate in the non-coherent L1).
+template <int W>
+__device__ __forceinline__ void stage_tiles(int L, const PassArgs &a, unsigned long long first, void *sm, int lane) {
+    typedef typename Traits<W>::E E;
+    E *s = reinterpret_cast<E *>(sm);
+#define MQ_STAGE(LL)                                                                      \
+    if (W == 2) ntt_detail::load_tiles_async<W, LL, PT>(a, first, s, lane);               \
+    else ntt_detail::load_tiles_sync<W, LL, PT>(a, first, s, lane);                        \
+    break;
+    switch (L) {
+    case 6: MQ_STAGE(6)
+    case 7: MQ_STAGE(7)
+    case 8: MQ_STAGE(8)
+    case 9: MQ_STAGE(9)
+    case 10: MQ_STAGE(10)
+    default: MQ_STAGE(11)
+    }
+#undef MQ_STAGE
+}
+
+template <int W, bool INV>
+__device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned long long first, void *sm, int tid) {
+    typedef typename Traits<W>::E E;
+    E *s = reinterpret_cast<E *>(sm);
+    switch (L) {
+    case 6: ntt_detail::tile_compute_store<W, 6, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 7: ntt_detail::tile_compute_store<W, 7, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 8: ntt_detail::tile_compute_store<W, 8, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 9: ntt_detail::tile_compute_store<W, 9, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 10: ntt_detail::tile_compute_store<W, 10, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    default: ntt_detail::tile_compute_store<W, 11, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    }
+}
+
+// ctrs: [0] next item, [1] status, [2, 2 + njobs) per-job finished items, then per-polynomial
+// finished first-pass items of two-pass transforms.
+//
+// Warp-specialised: warp 8 is the producer.  For item k it waits until buffer k % 2 is free,
+// takes the next item index, waits (bounded) for the item's dependencies, copies its arguments
+// and stages its tiles into the buffer, and hands it over.  Warps 0-7 compute and store the item,
+// publish its completion on the counters, and free the buffer.  The producer therefore runs one
+// item ahead, and its waits and loads overlap the transform of the previous item.
+__global__ void __launch_bounds__(CT, 2)
+    persistent_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
+                      unsigned *ctrs, unsigned njobs, unsigned long long limit_ns, size_t buf_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PassArgs s_pa[2];
+    __shared__ BlasArgs s_ba[2];
+    __shared__ unsigned s_it[2];
+    const int tid = threadIdx.x;
+    unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
+
+    if (tid >= BT) {  // ------------------------------------------------ producer warp
+        const int lane = tid - BT;
+        for (unsigned k = 0;; ++k) {
+            const int b = k & 1;
+            if (k >= 2) bar_sync(BAR_EMPTY + b);
+            unsigned it = 0;
+            if (lane == 0) {
+                it = atomicAdd(ctrs, 1u);
+                if (ld_status(status) != 0) it = n_items;  // the batch failed: drain
+            }
+            it = __shfl_sync(0xffffffffu, it, 0);
+            bool ok = it < n_items;
+            ItemDev item;
+            const JobDev *J = jobs;
+            if (ok) {
+                item = items[it];
+                J = jobs + item.job;
+                int w = 1;
+                if (lane == 0) {
+                    if (J->kind == JK_NTT && J->twopass && item.pass == 1)
+                        w = wait_geq(poly_ctr + J->poly_base + item.poly, J->groups0, status, limit_ns);
+                    else if (item.pass == 0 && J->after >= 0)
+                        w = wait_geq(job_ctr + J->after, jobs[J->after].n_items, status, limit_ns);
+                    if (!w) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
+                }
+                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+            }
+            if (!ok) {  // end of the work (or a failed wait): tell the compute warps and stop
+                if (lane == 0) s_it[b] = n_items;
+                __threadfence_block();
+                bar_arrive(BAR_FULL + b);
+                break;
+            }
+            if (J->kind == JK_NTT) {
+                const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
+                unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
+                for (int w = lane; w < (int)(sizeof(PassArgs) / 4); w += PT) dst[w] = src[w];
+                unsigned char *buf = smem_raw + b * buf_bytes;
+                if (J->width == 1) stage_tiles<1>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
+                else stage_tiles<2>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
+                asm volatile("cp.async.wait_all;" ::: "memory");
+            } else {
+                const unsigned *src = reinterpret_cast<const unsigned *>(&J->ba);
+                unsigned *dst = reinterpret_cast<unsigned *>(&s_ba[b]);
+                for (int w = lane; w < (int)(sizeof(BlasArgs) / 4); w += PT) dst[w] = src[w];
+            }
+            if (lane == 0) s_it[b] = it;
+            __threadfence_block();
+            bar_arrive(BAR_FULL + b);
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------------- compute warps
+    for (unsigned k = 0;; ++k) {
+        const int b = k & 1;
+        bar_sync(BAR_FULL + b);
+        const unsigned it = s_it[b];
+        if (it >= n_items) break;
+        const ItemDev item = items[it];
+        const JobDev *J = jobs + item.job;
+        const int kind = J->kind;
+        unsigned char *buf = smem_raw + b * buf_bytes;
+        if (kind == JK_NTT) {
+            const int L = J->L[item.pass];
+            if (J->width == 1) {
+                if (J->inv) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<1, false>(L, s_pa[b], item.first, buf, tid);
+            } else {
+                if (J->inv) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<2, false>(L, s_pa[b], item.first, buf, tid);
+            }
+        } else {
+            const BlasArgs &ba = s_ba[b];
+            const unsigned long long begin = item.first * J->chunk;
+            const unsigned long long end = begin + J->chunk < ba.n ? begin + J->chunk : ba.n;
+            if (J->width == 1) run_blas<1>(J->op, ba, begin, end, tid);
+            else run_blas<2>(J->op, ba, begin, end, tid);
+            ntt_detail::tile_sync<BAR_COMPUTE, BT>();
+        }
+        // every compute thread's stores precede the barrier above; thread 0's release makes them
+        // visible (cumulatively) to whoever acquires the counters
+        if (tid == 0) {
+            __threadfence();
+            if (kind == JK_NTT && J->twopass && item.pass == 0) atomicAdd(poly_ctr + J->poly_base + item.poly, 1u);
+            atomicAdd(job_ctr + item.job, 1u);
+        }
+        __threadfence_block();
+        bar_arrive(BAR_EMPTY + b);
+    }
+}
+
+size_t kernel_smem() {
+    size_t m = 0;
+    m = std::max(m, Shape<2, 6>::SMEM);
+    m = std::max(m, Shape<2, 7>::SMEM);
+    m = std::max(m, Shape<2, 8>::SMEM);
+    m = std::max(m, Shape<2, 9>::SMEM);
+    m = std::max(m, Shape<2, 10>::SMEM);
+    m = std::max(m, Shape<2, 11>::SMEM);
+    return m;
+}
+
+// tiles of 2^L residues per CTA of 256 threads (the Shape rule for L <= 11)
+inline unsigned tiles_per_cta(int L) { return 1u << (11 - L); }
+
+}  // namespace batch_detail
+}  // namespace mq
+
+using namespace mq;
+using namespace mq::batch_detail;
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+
+struct mq_batch {
+    int device = 0;
+    std::vector<mq_job> shape;
+    std::vector<JobDev> hjobs;
+    std::vector<void *> scratch;  // per job (natural-order two-pass transforms), else nullptr
+    JobDev *djobs = nullptr;
+    JobDev *pinned_jobs = nullptr;
+    ItemDev *ditems = nullptr;
+    unsigned *dctrs = nullptr;
+    size_t n_ctrs = 0;
+    size_t n_items = 0, ntt_items = 0, blas_items = 0;
+    unsigned grid = 0;
+    size_t smem = 0;
+    unsigned long long limit_ns = 0;
+    mq_batch_opts opts{};
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr, staged = nullptr;
+    int *h_status = nullptr;
+    bool launched = false;
+};
+
+static int job_passes(const mq_job &j) {
+    if (j.kind == MQ_JOB_NTT_FORWARD || j.kind == MQ_JOB_NTT_INVERSE) return j.plan->log2n <= 11 ? 1 : 2;
+    return 1;
+}
+
+static bool is_ntt(int kind) { return kind == MQ_JOB_NTT_FORWARD || kind == MQ_JOB_NTT_INVERSE; }
+
+static int blas_op_of(int kind) {
+    switch (kind) {
+    case MQ_JOB_VADD: return OP_VADD;
+    case MQ_JOB_VSUB: return OP_VSUB;
+    case MQ_JOB_VMUL: return OP_VMUL;
+    default: return OP_AXPY;
+    }
+}
+
+// Validate one job and fill its device descriptor (pointers, constants).  `scr` is the job's
+// staging buffer (natural-order two-pass transforms only).
+static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void *scr, JobDev &d) {
+    memset(&d, 0, sizeof d);
+    if (j.after >= (int)index) return mq_fail(MQ_ERR_ARG, "job %zu: `after` must name an earlier job", index);
+    if (j.after < -1) return mq_fail(MQ_ERR_ARG, "job %zu: bad `after`", index);
+    d.after = j.after;
+    if (is_ntt(j.kind)) {
+        const ntt_plan *p = j.plan;
+        if (!p) return mq_fail(MQ_ERR_ARG, "job %zu: NTT job without a plan", index);
+        if (p->log2n < LMIN || p->log2n > 2 * LMAX)
+            return mq_fail(MQ_ERR_SIZE, "job %zu: batched transforms need 2^%d <= N <= 2^%d", index, LMIN, 2 * LMAX);
+        if (!j.data) return mq_fail(MQ_ERR_ARG, "job %zu: data is NULL", index);
+        if (((uintptr_t)j.data) % 16) return mq_fail(MQ_ERR_ALIGN, "job %zu: data is not 16-byte aligned", index);
+        const size_t N = (size_t)1 << p->log2n;
+        const size_t batch = j.batch ? j.batch : 1;
+        const size_t stride = batch == 1 ? N : j.stride;
+        if (stride < N) return mq_fail(MQ_ERR_SIZE, "job %zu: stride shorter than N", index);
+        const bool inv = j.kind == MQ_JOB_NTT_INVERSE;
+        const bool natural = !(p->flags & MQ_ORDER_BITREV);
+        const int logN = (int)p->log2n;
+        d.kind = JK_NTT;
+        d.width = p->width;
+        d.inv = inv;
+        d.twopass = logN > LMAX;
+        const int L1 = d.twopass ? logN / 2 : 0, L2 = logN - L1;
+        for (int k = 0; k < 2; ++k) {
+            PassArgs &a = d.pa[k];
+            a.tw = inv ? p->tw_inv : p->tw_fwd;
+            memcpy(a.q, p->q, sizeof a.q);
+            memcpy(a.sc, p->sc, sizeof a.sc);
+            memcpy(a.scp, p->scp, sizeof a.scp);
+            memcpy(a.ws, p->ws, sizeof a.ws);
+            memcpy(a.wsp, p->wsp, sizeof a.wsp);
+            a.batch = batch;
+            a.logN = logN;
+            a.L1 = L1;
+        }
+        if (!d.twopass) {
+            PassArgs &a = d.pa[0];
+            a.in = a.out = j.data;
+            a.in_stride = a.out_stride = stride;
+            a.in_layout = (inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
+            a.out_layout = (!inv && natural) ? LAYOUT_NAT : LAYOUT_ROW;
+            a.scale = inv;
+            a.final = 1;
+            d.L[0] = logN;
+        } else {
+            PassArgs &first = d.pa[0], &second = d.pa[1];
+            PassArgs &col = inv ? second : first, &row = inv ? first : second;
+            col.col = 1;
+            col.in_layout = col.out_layout = LAYOUT_COL;
+            row.col = 0;
+            row.perm = natural;
+            if (!inv) {
+                col.in = j.data;
+                col.in_stride = stride;
+                col.out = natural ? scr : j.data;
+                col.out_stride = natural ? N : stride;
+                row.in = col.out;
+                row.in_stride = col.out_stride;
+                row.out = j.data;
+                row.out_stride = stride;
+                row.in_layout = LAYOUT_ROW;
+                row.out_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+                row.final = 1;
+                d.L[0] = L1;
+                d.L[1] = L2;
+            } else {
+                row.in = j.data;
+                row.in_stride = stride;
+                row.out = natural ? scr : j.data;
+                row.out_stride = natural ? N : stride;
+                row.in_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+                row.out_layout = LAYOUT_ROW;
+                col.in = row.out;
+                col.in_stride = row.out_stride;
+                col.out = j.data;
+                col.out_stride = stride;
+                col.scale = 1;
+                col.final = 1;
+                d.L[0] = L2;
+                d.L[1] = L1;
+            }
+        }
+        return MQ_OK;
+    }
+    if (j.kind < MQ_JOB_VADD || j.kind > MQ_JOB_AXPY) return mq_fail(MQ_ERR_ARG, "job %zu: unknown kind %d", index, j.kind);
+    hm::u128 Q;
+    int rc = mq_check_modulus(j.q, j.width, &Q);
+    if (rc) return rc;
+    if (j.n == 0) return mq_fail(MQ_ERR_ARG, "job %zu: empty vector", index);
+    const void *ptrs[3] = {j.data, j.a, j.kind == MQ_JOB_AXPY ? j.data : j.b};
+    for (int k = 0; k < 3; ++k) {
+        if (!ptrs[k]) return mq_fail(MQ_ERR_ARG, "job %zu: NULL operand", index);
+        if (((uintptr_t)ptrs[k]) % 16) return mq_fail(MQ_ERR_ALIGN, "job %zu: operands must be 16-byte aligned", index);
+    }
+    d.kind = JK_BLAS;
+    d.width = j.width;
+    d.op = blas_op_of(j.kind);
+    d.chunk = o.blas_chunk;
+    BlasArgs &b = d.ba;
+    b.c = j.data;
+    b.a = j.a;
+    b.b = ptrs[2];
+    b.n = j.n;
+    memcpy(b.q, j.q, sizeof b.q);
+    b.L = hm::bitlen(Q);
+    hm::to_words(hm::barrett_mu(Q, b.L), b.mu);
+    if (j.kind == MQ_JOB_AXPY) {
+        hm::u128 s = hm::from_words(j.scalar);
+        if (s >= Q || (j.width == MQ_W64 && j.scalar[1])) return mq_fail(MQ_ERR_RANGE, "job %zu: scalar must be < q", index);
+        hm::to_words(s, b.s);
+        hm::to_words(hm::shoup(s, Q, j.width == MQ_W64 ? 64 : 128), b.sp);
+    }
+    return MQ_OK;
+}
+
+static bool same_shape(const mq_job &a, const mq_job &b) {
+    if (a.kind != b.kind || a.after != b.after) return false;
+    if (is_ntt(a.kind)) {
+        if (!b.plan || a.plan->log2n != b.plan->log2n || a.plan->width != b.plan->width ||
+            (a.plan->flags & MQ_ORDER_BITREV) != (b.plan->flags & MQ_ORDER_BITREV))
+            return false;
+        return (a.batch ? a.batch : 1) == (b.batch ? b.batch : 1);
+    }
+    return a.n == b.n && a.width == b.width;
+}
+
+static void defaults(mq_batch_opts &o) {
+    if (o.lag == 0) o.lag = 4;
+    if (o.blas_chunk == 0) o.blas_chunk = 16384;
+    o.blas_chunk = (o.blas_chunk + 2047) / 2048 * 2048;
+    if (o.wait_timeout_s <= 0) o.wait_timeout_s = 2.0;
+}
+
+static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o);
+
+static void destroy_batch(mq_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->pinned_jobs) cudaFreeHost(b->pinned_jobs);
+    if (b->djobs) cudaFree(b->djobs);
+    if (b->ditems) cudaFree(b->ditems);
+    if (b->dctrs) cudaFree(b->dctrs);
+    for (void *p : b->scratch)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+static int enqueue_run(mq_batch *b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->dctrs, 0, b->n_ctrs * sizeof(unsigned), s);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "counter reset");
+    persistent_kernel<<<b->grid, CT, 2 * b->smem, s>>>(b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs,
+                                                      (unsigned)b->hjobs.size(), b->limit_ns, b->smem);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
+    e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "status copy");
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs, const mq_batch_opts *opts, void *stream) {
+    if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!jobs || njobs == 0) return mq_fail(MQ_ERR_ARG, "a batch needs at least one job");
+    if (njobs > (1u << 24)) return mq_fail(MQ_ERR_ARG, "too many jobs");
+    mq_batch *b = new mq_batch();
+    cudaGetDevice(&b->device);
+    b->shape.assign(jobs, jobs + njobs);
+    if (opts) {
+        b->opts = *opts;
+    } else {
+        lookup_tuned(b->shape, b->opts);
+    }
+    defaults(b->opts);
+    b->limit_ns = (unsigned long long)(b->opts.wait_timeout_s * 1e9);
+    b->hjobs.resize(njobs);
+    b->scratch.assign(njobs, nullptr);
+
+    // staging for natural-order two-pass transforms
+    for (size_t i = 0; i < njobs; ++i) {
+        const mq_job &j = jobs[i];
+        if (is_ntt(j.kind) && j.plan && j.plan->log2n > LMAX && j.plan->log2n <= 2 * LMAX &&
+            !(j.plan->flags & MQ_ORDER_BITREV)) {
+            size_t bytes = (j.batch ? j.batch : 1) * ((size_t)1 << j.plan->log2n) * 8u * (size_t)j.plan->width;
+            cudaError_t e = cudaMalloc(&b->scratch[i], bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                destroy_batch(b);
+                return mq_fail(MQ_ERR_OOM, "job %zu: staging of %zu bytes does not fit", i, bytes);
+            }
+        }
+    }
+    for (size_t i = 0; i < njobs; ++i) {
+        int rc = fill_job(jobs[i], i, b->opts, b->scratch[i], b->hjobs[i]);
+        if (rc) {
+            destroy_batch(b);
+            return rc;
+        }
+    }
+
+    // expand into items, ordered by the pipelining key
+    struct Key {
+        unsigned long long key;
+        unsigned stage, chain;
+        ItemDev it;
+    };
+    std::vector<Key> keys;
+    std::vector<unsigned> chain(njobs), depth(njobs);
+    unsigned next_chain = 0, poly_ctrs = 0;
+    bool dropped = !(b->opts.flags & MQ_BATCH_TEST_DROP_ITEM);
+    long drop_job = -1;
+    for (size_t i = 0; i < njobs; ++i) {
+        const mq_job &j = jobs[i];
+        JobDev &d = b->hjobs[i];
+        if (j.after < 0) {
+            chain[i] = next_chain++;
+            depth[i] = 0;
+        } else {
+            chain[i] = chain[j.after];
+            depth[i] = depth[j.after] + (unsigned)job_passes(jobs[j.after]);
+        }
+        unsigned count = 0;
+        auto push = [&](unsigned pass, unsigned poly, unsigned long long first) {
+            Key k;
+            k.stage = depth[i] + pass;
+            k.chain = chain[i];
+            k.key = (unsigned long long)k.chain + (unsigned long long)k.stage * b->opts.lag;
+            k.it.job = (unsigned)i;
+            k.it.pass = pass;
+            k.it.poly = poly;
+            k.it.pad = 0;
+            k.it.first = first;
+            if (!dropped && is_ntt(j.kind) && d.twopass && pass == 0) {
+                dropped = true;  // fault injection: this item never runs
+                drop_job = (long)i;
+            } else {
+                keys.push_back(k);
+                ++count;
+            }
+        };
+        if (d.kind == JK_NTT) {
+            const unsigned long long batch = d.pa[0].batch;
+            if (!d.twopass) {
+                const unsigned G = tiles_per_cta(d.L[0]);
+                for (unsigned long long t = 0; t < batch; t += G) push(0, 0, t);
+                b->ntt_items += (batch + G - 1) / G;
+            } else {
+                d.poly_base = poly_ctrs;
+                poly_ctrs += (unsigned)batch;
+                for (int pass = 0; pass < 2; ++pass) {
+                    const PassArgs &a = d.pa[pass];
+                    const unsigned TP = a.col ? (1u << (a.logN - a.L1)) : (1u << a.L1);
+                    const unsigned G = tiles_per_cta(d.L[pass]);
+                    const unsigned groups = TP / G;
+                    if (pass == 0) d.groups0 = groups;
+                    for (unsigned long long p = 0; p < batch; ++p)
+                        for (unsigned g = 0; g < groups; ++g) push(pass, (unsigned)p, p * TP + (unsigned long long)g * G);
+                    b->ntt_items += batch * groups;
+                }
+            }
+        } else {
+            const unsigned long long chunks = (d.ba.n + d.chunk - 1) / d.chunk;
+            for (unsigned long long c = 0; c < chunks; ++c) push(0, 0, c);
+            b->blas_items += chunks;
+        }
+        d.n_items = count;
+        if (keys.size() > 0xffffffffull) {
+            destroy_batch(b);
+            return mq_fail(MQ_ERR_SIZE, "more than 2^32 work items");
+        }
+    }
+    // a dropped item still counts toward its job's target: nothing can complete that job
+    if (drop_job >= 0) b->hjobs[drop_job].n_items += 1;
+    std::stable_sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) {
+        if (x.key != y.key) return x.key < y.key;
+        if (x.stage != y.stage) return x.stage < y.stage;
+        return x.chain < y.chain;
+    });
+    std::vector<ItemDev> items(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) items[k] = keys[k].it;
+    b->n_items = items.size();
+    b->n_ctrs = 2 + njobs + poly_ctrs;
+
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->djobs, njobs * sizeof(JobDev))) != cudaSuccess ||
+        (e = cudaMalloc(&b->ditems, std::max<size_t>(1, items.size()) * sizeof(ItemDev))) != cudaSuccess ||
+        (e = cudaMalloc(&b->dctrs, b->n_ctrs * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMallocHost(&b->pinned_jobs, njobs * sizeof(JobDev))) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_status, sizeof(int))) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_batch(b);
+        return mq_fail(MQ_ERR_OOM, "batch tables do not fit");
+    }
+    *b->h_status = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    memcpy(b->pinned_jobs, b->hjobs.data(), njobs * sizeof(JobDev));
+    if ((e = cudaMemcpyAsync(b->djobs, b->pinned_jobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->ditems, items.data(), items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        destroy_batch(b);
+        return mq_cuda_fail(e, "batch table upload");
+    }
+
+    // one wave of persistent CTAs
+    b->smem = kernel_smem();
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
+        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kernel_smem()));
+    });
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, CT, 2 * b->smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        destroy_batch(b);
+        return mq_fail(MQ_ERR_CUDA, "the persistent kernel does not fit on an SM");
+    }
+    unsigned want = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
+    b->grid = (unsigned)sms * std::min<unsigned>(want, (unsigned)per_sm);
+
+    if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess) {
+        destroy_batch(b);
+        return mq_cuda_fail(e, "batch stream/events");
+    }
+    if (!(b->opts.flags & MQ_BATCH_NO_GRAPH)) {
+        if ((e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            destroy_batch(b);
+            return mq_cuda_fail(e, "graph capture");
+        }
+        int rc = enqueue_run(b, b->cs);
+        cudaError_t e2 = cudaStreamEndCapture(b->cs, &b->graph);
+        if (rc || e2 != cudaSuccess) {
+            destroy_batch(b);
+            return rc ? rc : mq_cuda_fail(e2, "graph capture");
+        }
+        if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
+            destroy_batch(b);
+            return mq_cuda_fail(e, "graph instantiate");
+        }
+    }
+    *out = b;
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, void *stream) {
+    if (!b || !jobs) return mq_fail(MQ_ERR_ARG, "NULL batch or jobs");
+    if (njobs != b->shape.size()) return mq_fail(MQ_ERR_ARG, "the batch has %zu jobs, got %zu", b->shape.size(), njobs);
+    for (size_t i = 0; i < njobs; ++i)
+        if (!same_shape(b->shape[i], jobs[i])) return mq_fail(MQ_ERR_ARG, "job %zu differs in shape from the batch's", i);
+    std::vector<JobDev> next(njobs);
+    for (size_t i = 0; i < njobs; ++i) {
+        int rc = fill_job(jobs[i], i, b->opts, b->scratch[i], next[i]);
+        if (rc) return rc;
+        // counters and item bookkeeping stay those of the creation
+        next[i].n_items = b->hjobs[i].n_items;
+        next[i].poly_base = b->hjobs[i].poly_base;
+        next[i].groups0 = b->hjobs[i].groups0;
+    }
+    cudaError_t e = cudaEventSynchronize(b->staged);  // the previous upload has left the staging buffer
+    if (e != cudaSuccess) return mq_cuda_fail(e, "staging wait");
+    b->hjobs = next;
+    memcpy(b->pinned_jobs, b->hjobs.data(), njobs * sizeof(JobDev));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(b->djobs, b->pinned_jobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaEventRecord(b->staged, s)) != cudaSuccess)
+        return mq_cuda_fail(e, "job table upload");
+    for (size_t i = 0; i < njobs; ++i) b->shape[i] = jobs[i];
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_launch(mq_batch *b, void *stream) {
+    if (!b) return mq_fail(MQ_ERR_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (b->exec) {
+        e = cudaGraphLaunch(b->exec, s);
+        if (e != cudaSuccess) return mq_cuda_fail(e, "graph launch");
+    } else {
+        int rc = enqueue_run(b, s);
+        if (rc) return rc;
+    }
+    e = cudaEventRecord(b->done, s);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "event record");
+    b->launched = true;
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_status(mq_batch *b) {
+    if (!b) return mq_fail(MQ_ERR_ARG, "batch is NULL");
+    if (!b->launched) return MQ_OK;
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "batch wait");
+    int st = *(volatile int *)b->h_status;
+    if (st != 0) return mq_fail(st, "a device-side wait of the batch gave up after %.3f s", b->opts.wait_timeout_s);
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_info(const mq_batch *b, size_t *items, unsigned *ctas, size_t *ntt_items, size_t *blas_items) {
+    if (!b) return mq_fail(MQ_ERR_ARG, "batch is NULL");
+    if (items) *items = b->n_items;
+    if (ctas) *ctas = b->grid;
+    if (ntt_items) *ntt_items = b->ntt_items;
+    if (blas_items) *blas_items = b->blas_items;
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_destroy(mq_batch *b) {
+    destroy_batch(b);
+    return MQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// autotuner
+// ------------------------------------------------------------------------------------------------
+
+static uint64_t fnv1a(const std::string &s) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Key: device name and the batch shape (kinds, sizes, widths, dependencies), hashed.
+static std::string shape_key(const std::vector<mq_job> &jobs) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof prop);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string sig;
+    char buf[96];
+    for (const mq_job &j : jobs) {
+        if (is_ntt(j.kind))
+            snprintf(buf, sizeof buf, "%d:%u:%d:%u:%zu:%d;", j.kind, j.plan ? j.plan->log2n : 0, j.plan ? j.plan->width : 0,
+                     j.plan ? j.plan->flags : 0, j.batch, j.after);
+        else
+            snprintf(buf, sizeof buf, "%d:%zu:%d:%d;", j.kind, j.n, j.width, j.after);
+        sig += buf;
+    }
+    char key[160];
+    snprintf(key, sizeof key, "%s|%zu|%016llx", prop.name, jobs.size(), (unsigned long long)fnv1a(sig));
+    for (char *c = key; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return key;
+}
+
+static std::string read_file(const char *path) {
+    std::string s;
+    FILE *f = fopen(path, "rb");
+    if (!f) return s;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
+    fclose(f);
+    return s;
+}
+
+// The cache is a JSON object of "key": {"ctas_per_sm": c, "lag": l, "blas_chunk": b, "ms": t}.
+static bool cache_get(const char *path, const std::string &key, mq_batch_opts &o) {
+    std::string s = read_file(path);
+    size_t at = s.find("\"" + key + "\"");
+    if (at == std::string::npos) return false;
+    unsigned c = 0, l = 0, bc = 0;
+    if (sscanf(s.c_str() + at + key.size() + 2, " : {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u", &c, &l, &bc) != 3)
+        return false;
+    o.ctas_per_sm = c;
+    o.lag = l;
+    o.blas_chunk = bc;
+    return true;
+}
+
+static void cache_put(const char *path, const std::string &key, const mq_batch_opts &o, double ms) {
+    std::string s = read_file(path);
+    std::vector<std::string> entries;
+    // keep every other entry: one per line between the braces
+    size_t pos = 0;
+    while ((pos = s.find("\n  \"", pos)) != std::string::npos) {
+        size_t end = s.find('}', pos);
+        if (end == std::string::npos) break;
+        std::string line = s.substr(pos + 3, end + 1 - (pos + 3));
+        if (line.compare(0, key.size() + 2, "\"" + key + "\"") != 0) entries.push_back(line);
+        pos = end;
+    }
+    char buf[512];
+    snprintf(buf, sizeof buf, "\"%s\": {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"ms\": %.4f}", key.c_str(),
+             o.ctas_per_sm, o.lag, o.blas_chunk, ms);
+    entries.push_back(buf);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    fputs("{", f);
+    for (size_t i = 0; i < entries.size(); ++i) fprintf(f, "%s\n  %s", i ? "," : "", entries[i].c_str());
+    fputs("\n}\n", f);
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o) {
+    const char *path = getenv("MQNTT_TUNE_CACHE");
+    if (!path || !*path) return 0;
+    return cache_get(path, shape_key(jobs), o) ? 1 : 0;
+}
+
+extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts *best, const char *cache_path, void *stream) {
+    if (!jobs || !njobs || !best) return mq_fail(MQ_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool has_blas = false, has_deps = false;
+    for (size_t i = 0; i < njobs; ++i) {
+        has_blas |= !is_ntt(jobs[i].kind);
+        has_deps |= jobs[i].after >= 0 || (is_ntt(jobs[i].kind) && jobs[i].plan && jobs[i].plan->log2n > LMAX);
+    }
+    const unsigned ctas[] = {1, 2};
+    const unsigned lags[] = {1, 2, 4, 8, 16};
+    const unsigned chunks[] = {8192, 16384, 65536};
+    double best_ms = 1e30;
+    mq_batch_opts bo{};
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    int rc = MQ_OK;
+    for (unsigned c : ctas)
+        for (unsigned l : lags) {
+            if (!has_deps && l != 4) continue;
+            for (unsigned ch : chunks) {
+                if (!has_blas && ch != 16384) continue;
+                mq_batch_opts o{};
+                o.ctas_per_sm = c;
+                o.lag = l;
+                o.blas_chunk = ch;
+                mq_batch *b = nullptr;
+                rc = mq_batch_create(&b, jobs, njobs, &o, stream);
+                if (rc) goto done;
+                float ms = 0, sum = 0;
+                for (int r = 0; r < 2; ++r) mq_batch_launch(b, stream);  // warm-up
+                for (int r = 0; r < 5; ++r) {
+                    cudaEventRecord(t0, s);
+                    mq_batch_launch(b, stream);
+                    cudaEventRecord(t1, s);
+                    cudaEventSynchronize(t1);
+                    cudaEventElapsedTime(&ms, t0, t1);
+                    sum += ms;
+                }
+                rc = mq_batch_status(b);
+                mq_batch_destroy(b);
+                if (rc) goto done;
+                if (sum / 5 < best_ms) {
+                    best_ms = sum / 5;
+                    bo = o;
+                }
+            }
+        }
+    *best = bo;
+    defaults(*best);
+    if (cache_path && *cache_path) cache_put(cache_path, shape_key(std::vector<mq_job>(jobs, jobs + njobs)), *best, best_ms);
+done:
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return rc;
+}

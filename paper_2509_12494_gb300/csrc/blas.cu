@@ -8,6 +8,7 @@
 // one fixed scalar.  Both return the same canonical residue as any exact method.
 #include <cuda_runtime.h>
 
+#include "blas_ops.cuh"
 #include "common.cuh"
 
 namespace mq {
@@ -18,22 +19,6 @@ constexpr int BLAS_UNROLL = 4;  // 16-byte vectors in flight per thread and iter
 
 __host__ __device__ __forceinline__ uint4 u4(const uint64_t v[2]) {
     return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
-}
-
-template <int OP>
-__device__ __forceinline__ uint4 op128(uint4 a, uint4 b, const Mod128 &m, uint4 s, uint4 sp) {
-    if (OP == OP_VADD) return add_mod(a, b, m.q);
-    if (OP == OP_VSUB) return sub_mod(a, b, m.q);
-    if (OP == OP_VMUL) return mul_mod_barrett(a, b, m);
-    return add_mod(mul_mod_shoup(a, s, sp, m.q), b, m.q);  // axpy: s*x + y with x = a, y = b
-}
-
-template <int OP>
-__device__ __forceinline__ uint64_t op64(uint64_t a, uint64_t b, const Mod64 &m, uint64_t s, uint64_t sp) {
-    if (OP == OP_VADD) return add_mod(a, b, m.q);
-    if (OP == OP_VSUB) return sub_mod(a, b, m.q);
-    if (OP == OP_VMUL) return mul_mod_barrett(a, b, m);
-    return add_mod(mul_mod_shoup(a, s, sp, m.q), b, m.q);
 }
 
 template <int OP>

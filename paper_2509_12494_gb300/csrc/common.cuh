@@ -41,6 +41,7 @@ struct PassArgs {
     int perm;            // rows only: tiles are picked so that brv_L1(h) is contiguous (natural order)
     int in_layout, out_layout;
     int scale;           // inverse only: fold N^-1 into global stage 0
+    int final;           // last pass of the transform: store canonical residues
 };
 
 // Launch one pass; returns a cudaError_t.  L = log2 of the tile size, inv = direction.

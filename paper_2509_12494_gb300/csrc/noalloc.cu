@@ -84,6 +84,7 @@ extern "C" int ntt_forward_noalloc(const ntt_plan *p, void *d, size_t batch, siz
         a.in_stride = a.out_stride = stride;
         a.in_layout = LAYOUT_ROW;
         a.out_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+        a.final = 1;
         e = launch_ntt_pass(p->width, logN, false, a, s);
         return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "NTT pass launch");
     }
@@ -113,6 +114,7 @@ extern "C" int ntt_forward_noalloc(const ntt_plan *p, void *d, size_t batch, siz
     row.perm = natural;
     row.in_layout = LAYOUT_ROW;
     row.out_layout = natural ? LAYOUT_NAT : LAYOUT_ROW;
+    row.final = 1;
     e = launch_ntt_pass(p->width, L1, false, col, s);
     if (e == cudaSuccess) e = launch_ntt_pass(p->width, L2, false, row, s);
     return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "NTT pass launch");

@@ -68,7 +68,8 @@ struct Shape {
     static constexpr int R = T < 8 ? T : 8;          // residues per thread (radix)
     static constexpr int r = ilog2c(R);              // stages per register round
     static constexpr int TPT = T / R;                // threads per tile
-    static constexpr int G = (L <= 9) ? maxc(8, 256 / TPT) : (L == 10 ? 2 : 1);  // tiles per CTA
+    // tiles per CTA: 256 threads for tiles up to 2^11, 512 for 2^12
+    static constexpr int G = (L <= 11) ? (256 / TPT) : 1;
     static constexpr int NT = G * TPT;               // threads per CTA
     static constexpr int TS = T + 1;                 // padded tile stride in shared memory
     static constexpr int ROUNDS = (L + r - 1) / r;
@@ -97,137 +98,297 @@ __device__ __forceinline__ size_t tile_pos(int layout, unsigned ti, unsigned l, 
     return ((size_t)brv(l, L) << L1) + ti;
 }
 
-template <int W, int L, bool INV>
-__global__ void __launch_bounds__(Shape<W, L>::NT, (Shape<W, L>::NT <= 256) ? 2 : 1) ntt_pass_kernel(const PassArgs a) {
+__device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
+__device__ __forceinline__ uint4 ld_cg(const uint4 *p) { return __ldcg(p); }
+__device__ __forceinline__ void st_cg(uint64_t *p, uint64_t v) { __stcg((unsigned long long *)p, (unsigned long long)v); }
+__device__ __forceinline__ void st_cg(uint4 *p, uint4 v) { __stcg(p, v); }
+
+// Barrier among the NT threads that run the tile code: the whole CTA (id 0) or, in a kernel
+// with a separate producer warp, the named barrier BAR of the NT compute threads.
+template <int BAR, int NT>
+__device__ __forceinline__ void tile_sync() {
+    if (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
+// Per-tile addressing of one pass: for tile g of a CTA's group, the polynomial and the tile's
+// index inside it (tiles per polynomial are a power of two).
+struct TileAddr {
+    int lgTP;
+    unsigned long long mask;
+    __device__ __forceinline__ TileAddr(const PassArgs &a) {
+        lgTP = a.col ? (a.logN - a.L1) : a.L1;
+        mask = (1ull << lgTP) - 1;
+    }
+};
+
+// Stage tiles first_tile .. first_tile + G - 1 into `sm` with ordinary loads through L2.
+template <int W, int L, int NTH = Shape<W, L>::NT>
+__device__ __forceinline__ void load_tiles_sync(const PassArgs &a, unsigned long long first_tile,
+                                                typename Traits<W>::E *sm, int tid) {
+    typedef typename Traits<W>::E E;
+    typedef Shape<W, L> S;
+    const TileAddr ta(a);
+    const E *in = reinterpret_cast<const E *>(a.in);
+    const bool gfast = a.in_layout != LAYOUT_ROW;
+    constexpr int PER = (S::G * S::T) / NTH;       // residues per thread
+    constexpr int BATCH = PER < 16 ? PER : 16;      // loads in flight per thread
+    static_assert(PER % BATCH == 0, "tile residues must split evenly");
+#pragma unroll 1
+    for (int c = 0; c < PER; c += BATCH) {
+        E v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int i = tid + (c + u) * NTH;
+            int g = gfast ? (i % S::G) : (i / S::T);
+            int l = gfast ? (i / S::G) : (i % S::T);
+            unsigned long long gt = first_tile + g;
+            unsigned long long poly = gt >> ta.lgTP;
+            unsigned ti = (unsigned)(gt & ta.mask);
+            v[u] = poly < a.batch ? ld_cg(in + poly * a.in_stride + tile_pos(a.in_layout, ti, l, L, a.L1, a.logN, a.perm))
+                                  : E();
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int i = tid + (c + u) * NTH;
+            int g = gfast ? (i % S::G) : (i / S::T);
+            int l = gfast ? (i / S::G) : (i % S::T);
+            sm[g * S::TS + swz<W>(l)] = v[u];
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async(void *dst, const uint4 *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async(void *dst, const uint64_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// The same staging with asynchronous copies (cp.async): the caller commits the group and waits
+// for it before the tiles are used.  Tiles past the last polynomial are left unfilled (their
+// results are never stored).
+template <int W, int L, int NTH = Shape<W, L>::NT>
+__device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned long long first_tile,
+                                                 typename Traits<W>::E *sm, int tid) {
+    typedef typename Traits<W>::E E;
+    typedef Shape<W, L> S;
+    const TileAddr ta(a);
+    const E *in = reinterpret_cast<const E *>(a.in);
+    const bool gfast = a.in_layout != LAYOUT_ROW;
+    for (int i = tid; i < S::G * S::T; i += NTH) {
+        int g = gfast ? (i % S::G) : (i / S::T);
+        int l = gfast ? (i / S::G) : (i % S::T);
+        unsigned long long gt = first_tile + g;
+        unsigned long long poly = gt >> ta.lgTP;
+        unsigned ti = (unsigned)(gt & ta.mask);
+        if (poly < a.batch)
+            cp_async(sm + g * S::TS + swz<W>(l), in + poly * a.in_stride + tile_pos(a.in_layout, ti, l, L, a.L1, a.logN, a.perm));
+    }
+}
+
+// One register round: stages s_begin .. s_begin + RR - 1 of a tile of 2^L residues, each thread
+// holding R residues (R / 2^RR independent groups of 2^RR), read from and written back to the
+// shared-memory tile, then a barrier.  s_begin is a runtime value so that all full rounds share
+// this code (the instruction footprint matters when several kernels' tiles share one SM).
+template <int W, int L, int RR, bool INV, int BAR = 0>
+__device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
+                                            int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
+                                            typename Traits<W>::E q2) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
     typedef Shape<W, L> S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    E *sm = reinterpret_cast<E *>(smem_raw);
-
-    const E q = Tr::make(a.q);
-    const int L1 = a.L1, logN = a.logN;
-    const unsigned TP = a.col ? (1u << (logN - L1)) : (1u << L1);  // tiles per polynomial
-    const unsigned long long first_tile = (unsigned long long)blockIdx.x * S::G;
-    const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
-    const E *in = reinterpret_cast<const E *>(a.in);
-    E *out = reinterpret_cast<E *>(a.out);
-    const bool gfast_in = a.in_layout != LAYOUT_ROW, gfast_out = a.out_layout != LAYOUT_ROW;
-
-    // ---- global -> shared (coalesced: consecutive threads take consecutive global residues)
-    for (int i = threadIdx.x; i < S::G * S::T; i += S::NT) {
-        int g = gfast_in ? (i % S::G) : (i / S::T);
-        int l = gfast_in ? (i / S::G) : (i % S::T);
-        unsigned long long gt = first_tile + g;
-        unsigned long long poly = gt / TP;
-        unsigned ti = (unsigned)(gt % TP);
-        E v;
-        if (poly < a.batch)
-            v = in[poly * a.in_stride + tile_pos(a.in_layout, ti, l, L, L1, logN, a.perm)];
-        else
-            v = E();
-        sm[g * S::TS + swz<W>(l)] = v;
-    }
-    __syncthreads();
-
-    // ---- register rounds of up to three stages
-    const int g = threadIdx.x / S::TPT, t = threadIdx.x % S::TPT;
-    unsigned tw_base;
-    {
-        unsigned long long gt = first_tile + g;
-        unsigned ti = (unsigned)(gt % TP);
-        tw_base = a.col ? 1u : ((1u << L1) + (a.perm ? brv(ti, L1) : ti));
-    }
-    E *tile = sm + g * S::TS;
+    constexpr int V = S::R >> RR;  // independent groups per thread
+    const int b_lo = L - s_begin - RR, b_hi = L - 1 - s_begin;
     E x[S::R];
-
+    int base[V];
 #pragma unroll
-    for (int rr_ = 0; rr_ < S::ROUNDS; ++rr_) {
-        const int rho = INV ? (S::ROUNDS - 1 - rr_) : rr_;
-        const int s_begin = rho * S::r;
-        const int s_end = (s_begin + S::r < L) ? s_begin + S::r : L;
-        const int rr = s_end - s_begin;  // stages in this round
-        const int b_hi = L - 1 - s_begin, b_lo = L - s_end;
-        const int V = S::R >> rr;        // independent groups per thread in this round
-        int base[S::R];
+    for (int k = 0; k < V; ++k) {
+        int vt = t + k * S::TPT;
+        int lo = vt & ((1 << b_lo) - 1), hi = vt >> b_lo;
+        base[k] = (hi << (b_hi + 1)) | lo;
+#pragma unroll
+        for (int e = 0; e < (1 << RR); ++e) x[k * (1 << RR) + e] = tile[swz<W>(base[k] | (e << b_lo))];
+    }
+#pragma unroll
+    for (int jj = 0; jj < RR; ++jj) {
+        const int j = INV ? (RR - 1 - jj) : jj;
+        const int s = s_begin + j;           // local stage
+        const int half = 1 << (RR - 1 - j);  // distance in the register index
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            int vt = t + k * S::TPT;
-            int lo = vt & ((1 << b_lo) - 1), hi = vt >> b_lo;
-            base[k] = (hi << (b_hi + 1)) | lo;
 #pragma unroll
-            for (int e = 0; e < (1 << rr); ++e) x[k * (1 << rr) + e] = tile[swz<W>(base[k] | (e << b_lo))];
-        }
-#pragma unroll
-        for (int jj = 0; jj < rr; ++jj) {
-            const int j = INV ? (rr - 1 - jj) : jj;
-            const int s = s_begin + j;                 // local stage
-            const int half = 1 << (rr - 1 - j);        // distance in the register index
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-#pragma unroll
-                for (int e0 = 0; e0 < (1 << rr); ++e0) {
-                    if (e0 & half) continue;
-                    const int l0 = base[k] | (e0 << b_lo);
-                    const unsigned idx = (tw_base << s) + ((unsigned)l0 >> (L - s));
-                    E &u = x[k * (1 << rr) + e0];
-                    E &v = x[k * (1 << rr) + e0 + half];
-                    E w, wp;
-                    if (!INV) {
-                        Tr::load_tw(tw, idx, w, wp);
-                        E tv = mul_mod_shoup(v, w, wp, q);
-                        E nu = add_mod(u, tv, q);
-                        v = sub_mod(u, tv, q);
-                        u = nu;
-                    } else if (s == 0 && a.scale) {
-                        E sum = add_mod(u, v, q), dif = sub_mod(u, v, q);
-                        u = mul_mod_shoup(sum, Tr::make(a.sc), Tr::make(a.scp), q);
-                        v = mul_mod_shoup(dif, Tr::make(a.ws), Tr::make(a.wsp), q);
-                    } else {
-                        Tr::load_tw(tw, idx, w, wp);
-                        E sum = add_mod(u, v, q), dif = sub_mod(u, v, q);
-                        u = sum;
-                        v = mul_mod_shoup(dif, w, wp, q);
-                    }
+            for (int e0 = 0; e0 < (1 << RR); ++e0) {
+                if (e0 & half) continue;
+                const int l0 = base[k] | (e0 << b_lo);
+                const unsigned idx = (tw_base << s) + ((unsigned)l0 >> (L - s));
+                E &u = x[k * (1 << RR) + e0];
+                E &v = x[k * (1 << RR) + e0 + half];
+                E w, wp;
+                if (!INV) {
+                    Tr::load_tw(tw, idx, w, wp);
+                    E uu = csub(u, q2);                              // [0, 2q)
+                    E tv = mul_mod_shoup_lazy(v, w, wp, q);          // [0, 2q)
+                    u = add_nored(uu, tv);                           // [0, 4q)
+                    v = add_sub(uu, q2, tv);                         // (0, 4q)
+                } else if (s == 0 && a.scale) {
+                    E dif = add_sub(u, q2, v);                       // (0, 4q)
+                    E sum = add_nored(u, v);                         // [0, 4q)
+                    u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q);
+                    v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q);
+                } else {
+                    Tr::load_tw(tw, idx, w, wp);
+                    E dif = add_sub(u, q2, v);                       // (0, 4q)
+                    u = csub(add_nored(u, v), q2);                   // [0, 2q)
+                    v = mul_mod_shoup_lazy(dif, w, wp, q);           // [0, 2q)
                 }
             }
         }
+    }
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
+    for (int k = 0; k < V; ++k) {
 #pragma unroll
-            for (int e = 0; e < (1 << rr); ++e) tile[swz<W>(base[k] | (e << b_lo))] = x[k * (1 << rr) + e];
-        }
-        __syncthreads();
+        for (int e = 0; e < (1 << RR); ++e) tile[swz<W>(base[k] | (e << b_lo))] = x[k * (1 << RR) + e];
+    }
+    tile_sync<BAR, S::NT>();
+}
+
+// One CTA's share of a pass on tiles already staged in `sm` (by load_tiles_*): tiles
+// first_tile .. first_tile + G - 1 of the batch, a tile past the last polynomial being skipped.
+// Called by NT = Shape::NT threads with thread index tid after a barrier that follows the staging;
+// ends with a barrier, after which `sm` may be refilled.
+//
+// Butterflies are lazy (Harvey): between stages the values stay below 4q (forward) or 2q
+// (inverse) and Shoup products skip their final correction; the pass flagged `final`
+// canonicalises what it stores.  q < 2^124 (2^60) keeps 4q below the word size.
+//   forward (CT):  u <- u mod 2q;  t = w v mod q + {0, q};  (u, v) <- (u + t, u + 2q - t)
+//   inverse (GS):  (u, v) <- ((u + v) mod 2q, (u + 2q - v) w mod q + {0, q})
+// Global loads and stores go through L2 only (.cg), so a pass may read what another SM wrote
+// earlier in the same kernel once the writer's completion is observed.
+template <int W, int L, bool INV, int BAR = 0>
+__device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned long long first_tile,
+                                           typename Traits<W>::E *sm, int tid) {
+    typedef Traits<W> Tr;
+    typedef typename Tr::E E;
+    typedef Shape<W, L> S;
+
+    const E q = Tr::make(a.q);
+    const E q2 = add_nored(q, q);
+    const int L1 = a.L1, logN = a.logN;
+    const TileAddr ta(a);
+    const int lgTP = ta.lgTP;
+    const unsigned long long tp_mask = ta.mask;
+    const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
+    E *out = reinterpret_cast<E *>(a.out);
+    const bool gfast_out = a.out_layout != LAYOUT_ROW;
+
+    // ---- register rounds: every full round (three stages) runs the same code in a loop; a
+    // shorter round, when L is not a multiple of 3, has its own (forward: last, inverse: first)
+    const int g = tid / S::TPT, t = tid % S::TPT;
+    unsigned tw_base;
+    {
+        unsigned long long gt = first_tile + g;
+        unsigned ti = (unsigned)(gt & tp_mask);
+        tw_base = a.col ? 1u : ((1u << L1) + (a.perm ? brv(ti, L1) : ti));
+    }
+    E *tile = sm + g * S::TS;
+    constexpr int FULL = L / S::r, PART = L - FULL * S::r;
+    if (!INV) {
+#pragma unroll 1
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q2);
+        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q2);
+    } else {
+        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q2);
+#pragma unroll 1
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q2);
     }
 
-    // ---- shared -> global
-    for (int i = threadIdx.x; i < S::G * S::T; i += S::NT) {
+    // ---- shared -> global (canonical residues from the last pass)
+    for (int i = tid; i < S::G * S::T; i += S::NT) {
         int gg = gfast_out ? (i % S::G) : (i / S::T);
         int l = gfast_out ? (i / S::G) : (i % S::T);
         unsigned long long gt = first_tile + gg;
-        unsigned long long poly = gt / TP;
-        unsigned ti = (unsigned)(gt % TP);
-        if (poly < a.batch)
-            out[poly * a.out_stride + tile_pos(a.out_layout, ti, l, L, L1, logN, a.perm)] = sm[gg * S::TS + swz<W>(l)];
+        unsigned long long poly = gt >> lgTP;
+        unsigned ti = (unsigned)(gt & tp_mask);
+        if (poly < a.batch) {
+            E v = sm[gg * S::TS + swz<W>(l)];
+            if (a.final) {
+                if (!INV) v = csub(v, q2);  // forward values are below 4q
+                v = csub(v, q);
+            }
+            st_cg(out + poly * a.out_stride + tile_pos(a.out_layout, ti, l, L, L1, logN, a.perm), v);
+        }
     }
+    tile_sync<BAR, S::NT>();
+}
+
+// The whole pass for one CTA group with synchronous staging (used by the batched kernel).
+template <int W, int L, bool INV>
+__device__ __forceinline__ void tile_group(const PassArgs &a, unsigned long long first_tile,
+                                           typename Traits<W>::E *sm, int tid) {
+    load_tiles_sync<W, L>(a, first_tile, sm, tid);
+    __syncthreads();
+    tile_compute_store<W, L, INV>(a, first_tile, sm, tid);
+}
+
+// A pass over `groups` CTA groups by a persistent grid: each CTA walks the groups with a stride
+// of gridDim.x and prefetches the next group's tiles (cp.async into the second of two shared
+// buffers) while it transforms the current one.
+template <int W, int L, bool INV>
+__global__ void __launch_bounds__(Shape<W, L>::NT, (Shape<W, L>::NT <= 256) ? 3 : 1)
+    ntt_pass_kernel(const PassArgs a, unsigned long long groups) {
+    typedef typename Traits<W>::E E;
+    typedef Shape<W, L> S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    E *buf0 = reinterpret_cast<E *>(smem_raw), *buf1 = buf0 + S::G * S::TS;
+    const int tid = threadIdx.x;
+    unsigned long long grp = blockIdx.x;
+    if (grp < groups) load_tiles_async<W, L>(a, grp * S::G, buf0, tid);
+    cp_async_commit();
+    bool odd = false;
+    for (; grp < groups; grp += gridDim.x) {
+        E *cur = odd ? buf1 : buf0, *nxt = odd ? buf0 : buf1;
+        const unsigned long long next = grp + gridDim.x;
+        if (next < groups) load_tiles_async<W, L>(a, next * S::G, nxt, tid);
+        cp_async_commit();
+        cp_async_wait_1();  // this thread's copies of the current group have landed
+        __syncthreads();    // and everyone else's
+        tile_compute_store<W, L, INV>(a, grp * S::G, cur, tid);
+        odd = !odd;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <int W, int L, bool INV>
 cudaError_t launch_one(const PassArgs &a, cudaStream_t s) {
     typedef Shape<W, L> S;
-    static bool configured = false;  // benign race: every thread sets the same attribute
-    if (!configured) {
+    static int per_sm = 0;  // benign race: every thread computes the same values
+    const size_t smem = 2 * S::SMEM;
+    if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<W, L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::SMEM);
+                                             (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ntt_pass_kernel<W, L, INV>, S::NT, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = n > 0 ? n : 1;
     }
     const unsigned long long TP = a.col ? (1ull << (a.logN - a.L1)) : (1ull << a.L1);
     const unsigned long long tiles = TP * a.batch;
-    const unsigned long long grid = (tiles + S::G - 1) / S::G;
-    if (grid == 0) return cudaSuccess;
-    if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    ntt_pass_kernel<W, L, INV><<<(unsigned)grid, S::NT, S::SMEM, s>>>(a);
+    const unsigned long long groups = (tiles + S::G - 1) / S::G;
+    if (groups == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned long long wave = (unsigned long long)sms * per_sm;
+    const unsigned grid = (unsigned)(groups < wave ? groups : wave);
+    ntt_pass_kernel<W, L, INV><<<grid, S::NT, smem, s>>>(a, groups);
     return cudaGetLastError();
 }
 

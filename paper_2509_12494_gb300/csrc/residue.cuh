@@ -52,6 +52,13 @@ __device__ __forceinline__ uint64_t mul_mod_shoup(uint64_t a, uint64_t w, uint64
     return (r >= q) ? r - q : r;
 }
 
+__device__ __forceinline__ uint64_t mul_mod_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t q) {
+    return a * w - __umul64hi(a, wp) * q;  // in [0, 2q)
+}
+__device__ __forceinline__ uint64_t csub(uint64_t a, uint64_t m) { return a >= m ? a - m : a; }
+__device__ __forceinline__ uint64_t add_nored(uint64_t a, uint64_t b) { return a + b; }
+__device__ __forceinline__ uint64_t add_sub(uint64_t a, uint64_t b2, uint64_t c) { return a + b2 - c; }
+
 // a * b mod q for any a, b < q (Barrett, Sec. 2.1).
 __device__ __forceinline__ uint64_t mul_mod_barrett(uint64_t a, uint64_t b, const Mod64 &m) {
     uint64_t xlo = a * b, xhi = __umul64hi(a, b);           // x = a*b < 2^(2L)
@@ -126,51 +133,50 @@ __device__ __forceinline__ uint4 sub_mod(uint4 a, uint4 b, uint4 q) {
     return add128(d, and128(q, m));  // add q back only when a < b
 }
 
-// Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  Products of the even
-// limbs a0, a2 and of the odd limbs a1, a3 are accumulated in two carry chains whose lo/hi halves
-// land in alternating columns, then the two partial sums are added.
+// Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  The 16 limb products
+// are accumulated in two carry chains: E takes the products of the even limbs a0, a2 and O those
+// of the odd limbs a1, a3, so that within one row (one limb b_i) the lo and hi halves of a chain
+// land in consecutive columns.  Row 0 needs no additions; every later row ends in a fresh limb
+// (hi half plus the incoming carry, which cannot overflow), so no separate carry propagation is
+// needed.  A final 7-limb addition merges the two chains: 32 multiply instructions and 7 adds.
 __device__ __forceinline__ void mul_wide(const uint4 a, const uint4 b, uint32_t c[8]) {
-    uint32_t E[8] = {0, 0, 0, 0, 0, 0, 0, 0}, O[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint32_t bb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        // even limbs: lo(a0 bi)->i, hi(a0 bi)->i+1, lo(a2 bi)->i+2, hi(a2 bi)->i+3, carry->i+4
-        asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
-            "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
-            "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
-            "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
-            "addc.u32       %4, %4, 0;"
-            : "+r"(E[i]), "+r"(E[i + 1]), "+r"(E[i + 2]), "+r"(E[i + 3]), "+r"(E[i + 4])
-            : "r"(a.x), "r"(a.z), "r"(bb[i]));
-        // odd limbs: lo(a1 bi)->i+1, hi(a1 bi)->i+2, lo(a3 bi)->i+3, hi(a3 bi)->i+4, carry->i+5
-        if (i < 3) {
-            asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
-                "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
-                "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
-                "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
-                "addc.u32       %4, %4, 0;"
-                : "+r"(O[i + 1]), "+r"(O[i + 2]), "+r"(O[i + 3]), "+r"(O[i + 4]), "+r"(O[i + 5])
-                : "r"(a.y), "r"(a.w), "r"(bb[i]));
-        } else {  // the product is below 2^256: nothing carries out of limb 7
-            asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
-                "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
-                "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
-                "madc.hi.u32    %3, %5, %6, %3;"
-                : "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7])
-                : "r"(a.y), "r"(a.w), "r"(bb[3]));
-        }
-    }
-    c[0] = E[0];
-    asm("add.cc.u32  %0, %7, %14;\n\t"
-        "addc.cc.u32 %1, %8, %15;\n\t"
-        "addc.cc.u32 %2, %9, %16;\n\t"
-        "addc.cc.u32 %3, %10, %17;\n\t"
-        "addc.cc.u32 %4, %11, %18;\n\t"
-        "addc.cc.u32 %5, %12, %19;\n\t"
-        "addc.u32    %6, %13, %20;"
+    uint32_t E0, E1, E2, E3, E4, E5, E6, O1, O2, O3, O4, O5, O6, O7;
+    asm("mul.lo.u32 %0, %8, %12;\n\t"
+        "mul.hi.u32 %1, %8, %12;\n\t"
+        "mul.lo.u32 %2, %10, %12;\n\t"
+        "mul.hi.u32 %3, %10, %12;\n\t"
+        "mul.lo.u32 %4, %9, %12;\n\t"
+        "mul.hi.u32 %5, %9, %12;\n\t"
+        "mul.lo.u32 %6, %11, %12;\n\t"
+        "mul.hi.u32 %7, %11, %12;"
+        : "=r"(E0), "=r"(E1), "=r"(E2), "=r"(E3), "=r"(O1), "=r"(O2), "=r"(O3), "=r"(O4)
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x));
+#define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
+    asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
+        "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \
+        "madc.lo.cc.u32 %2, %10, %12, %2;\n\t"                                                \
+        "madc.hi.u32    %3, %10, %12, 0;\n\t"                                                 \
+        "mad.lo.cc.u32  %4, %9, %12, %4;\n\t"                                                 \
+        "madc.hi.cc.u32 %5, %9, %12, %5;\n\t"                                                 \
+        "madc.lo.cc.u32 %6, %11, %12, %6;\n\t"                                                \
+        "madc.hi.u32    %7, %11, %12, 0;"                                                       \
+        : "+r"(e0), "+r"(e1), "+r"(e2), "=r"(e3), "+r"(o1), "+r"(o2), "+r"(o3), "=r"(o4)       \
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(bi));
+    MQ_ROW(E1, E2, E3, E4, O2, O3, O4, O5, b.y)
+    MQ_ROW(E2, E3, E4, E5, O3, O4, O5, O6, b.z)
+    MQ_ROW(E3, E4, E5, E6, O4, O5, O6, O7, b.w)
+#undef MQ_ROW
+    c[0] = E0;
+    asm("add.cc.u32  %0, %7, %13;\n\t"
+        "addc.cc.u32 %1, %8, %14;\n\t"
+        "addc.cc.u32 %2, %9, %15;\n\t"
+        "addc.cc.u32 %3, %10, %16;\n\t"
+        "addc.cc.u32 %4, %11, %17;\n\t"
+        "addc.cc.u32 %5, %12, %18;\n\t"
+        "addc.u32    %6, %19, 0;"
         : "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
-        : "r"(E[1]), "r"(E[2]), "r"(E[3]), "r"(E[4]), "r"(E[5]), "r"(E[6]), "r"(E[7]), "r"(O[1]), "r"(O[2]),
-          "r"(O[3]), "r"(O[4]), "r"(O[5]), "r"(O[6]), "r"(O[7]));
+        : "r"(E1), "r"(E2), "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(O1), "r"(O2), "r"(O3), "r"(O4), "r"(O5),
+          "r"(O6), "r"(O7));
 }
 
 // Low 128 bits of a * b: only the products that reach columns 0..3.
@@ -222,6 +228,28 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
     uint32_t m;
     uint4 r = sub128(mul_lo(a, w), mul_lo(qhat, q), m);  // true remainder or + q; exact mod 2^128
     return reduce_once(r, q);
+}
+
+// a * w mod q up to one multiple of q: the result is in [0, 2q).  Shoup's quotient estimate is
+// the true quotient or one less, so skipping the final correction leaves at most one extra q.
+// a may be any value below 2^128 (lazy butterflies feed it values below 4q).
+__device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q) {
+    uint32_t h[8];
+    mul_wide(a, wp, h);
+    uint4 qhat = make_uint4(h[4], h[5], h[6], h[7]);
+    uint32_t m;
+    return sub128(mul_lo(a, w), mul_lo(qhat, q), m);
+}
+
+// a >= m ? a - m : a
+__device__ __forceinline__ uint4 csub(uint4 a, uint4 m) { return reduce_once(a, m); }
+
+__device__ __forceinline__ uint4 add_nored(uint4 a, uint4 b) { return add128(a, b); }
+
+// a + b2 - c for values that keep the result in [0, 2^128): b2 = 2q, c < 2q
+__device__ __forceinline__ uint4 add_sub(uint4 a, uint4 b2, uint4 c) {
+    uint32_t m;
+    return sub128(add128(a, b2), c, m);
 }
 
 // floor(c / 2^s) for an 8-limb c whose quotient fits in 128 bits; s uniform across the warp.

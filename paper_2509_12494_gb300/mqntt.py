@@ -64,6 +64,14 @@ def load(build_if_missing: bool = False):
         "mod_axpy": [_vp, _u64x2, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
         "mq_probe_imad_rate": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), _vp],
+        "mq_batch_create": [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _vp, _vp],
+        "mq_batch_update": [_vp, _vp, ctypes.c_size_t, _vp],
+        "mq_batch_launch": [_vp, _vp],
+        "mq_batch_status": [_vp],
+        "mq_batch_info": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint),
+                          ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+        "mq_batch_destroy": [_vp],
+        "mq_autotune_batch": [_vp, ctypes.c_size_t, _vp, ctypes.c_char_p, _vp],
         "mq_last_error": [],
         "mq_version": [],
     }
@@ -190,6 +198,97 @@ def mq_last_error() -> str:
 
 def mq_version() -> str:
     return load().mq_version().decode()
+
+
+# ------------------------------------------------------------------------- batches (mqntt_batch.h)
+
+MQ_JOB_NTT_FORWARD, MQ_JOB_NTT_INVERSE, MQ_JOB_VADD, MQ_JOB_VSUB, MQ_JOB_VMUL, MQ_JOB_AXPY = 1, 2, 3, 4, 5, 6
+MQ_BATCH_NO_GRAPH, MQ_BATCH_TEST_DROP_ITEM = 1, 2
+
+
+class mq_job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("after", ctypes.c_int), ("plan", _vp), ("data", _vp), ("a", _vp),
+                ("b", _vp), ("n", ctypes.c_size_t), ("batch", ctypes.c_size_t), ("stride", ctypes.c_size_t),
+                ("q", ctypes.c_uint64 * 2), ("scalar", ctypes.c_uint64 * 2), ("width", ctypes.c_int)]
+
+
+class mq_batch_opts(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_uint), ("lag", ctypes.c_uint), ("blas_chunk", ctypes.c_uint),
+                ("wait_timeout_s", ctypes.c_double), ("flags", ctypes.c_uint)]
+
+
+def ntt_job(kind: int, plan: Plan, data, batch: int = 1, stride: int = 0, after: int = -1) -> mq_job:
+    j = mq_job()
+    j.kind, j.after, j.plan, j.data, j.batch, j.stride = kind, after, plan.handle, ptr(data), batch, stride
+    return j
+
+
+def blas_job(kind: int, data, a, b, n: int, q: int, width: int, scalar: int = 0, after: int = -1) -> mq_job:
+    j = mq_job()
+    j.kind, j.after, j.data, j.a, j.b, j.n, j.width = kind, after, ptr(data), ptr(a), ptr(b), n, width
+    j.q = words(q)
+    j.scalar = words(scalar)
+    return j
+
+
+def _job_array(jobs):
+    arr = (mq_job * len(jobs))(*jobs)
+    return arr
+
+
+class Batch:
+    """Owns an mq_batch* (freed by mq_batch_destroy or on garbage collection)."""
+
+    def __init__(self, handle: int, njobs: int):
+        self.handle, self.njobs = handle, njobs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mq_batch_destroy(self.handle)
+            self.handle = None
+
+
+def mq_batch_create(jobs, opts: mq_batch_opts | None = None, stream=None) -> Batch:
+    h = _vp()
+    arr = _job_array(jobs)
+    _check(load().mq_batch_create(ctypes.byref(h), ctypes.cast(arr, _vp), len(jobs),
+                                  ctypes.cast(ctypes.byref(opts), _vp) if opts is not None else None,
+                                  stream_handle(stream)))
+    return Batch(h.value, len(jobs))
+
+
+def mq_batch_update(batch: Batch, jobs, stream=None):
+    arr = _job_array(jobs)
+    _check(load().mq_batch_update(batch.handle, ctypes.cast(arr, _vp), len(jobs), stream_handle(stream)))
+
+
+def mq_batch_launch(batch: Batch, stream=None):
+    _check(load().mq_batch_launch(batch.handle, stream_handle(stream)))
+
+
+def mq_batch_status(batch: Batch) -> int:
+    """Returns the status code (0 or MQ_ERR_TIMEOUT, ...) without raising."""
+    return load().mq_batch_status(batch.handle)
+
+
+def mq_batch_info(batch: Batch):
+    a, b, c, d = ctypes.c_size_t(), ctypes.c_uint(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().mq_batch_info(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return {"items": a.value, "ctas": b.value, "ntt_items": c.value, "blas_items": d.value}
+
+
+def mq_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(load().mq_batch_destroy(batch.handle))
+        batch.handle = None
+
+
+def mq_autotune_batch(jobs, cache_path: str | None = None, stream=None) -> mq_batch_opts:
+    best = mq_batch_opts()
+    arr = _job_array(jobs)
+    _check(load().mq_autotune_batch(ctypes.cast(arr, _vp), len(jobs), ctypes.byref(best),
+                                    cache_path.encode() if cache_path else None, stream_handle(stream)))
+    return best
 
 
 # ------------------------------------------------------------------------- tensor marshalling
