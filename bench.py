@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-blas", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
+    p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
     return p.parse_args()
 
 
@@ -161,7 +163,8 @@ def run_gpu(args, rank, world):
     # the persistent batch: job i = forward of polynomial i, job batch + i = its inverse
     jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
     jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
-    pbatch = M.mq_batch_create(jobs, stream=sh)
+    opts = M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm) if (args.lag or args.ctas_per_sm) else None
+    pbatch = M.mq_batch_create(jobs, opts, stream=sh)
     pinfo = M.mq_batch_info(pbatch)
 
     def step_batched():

@@ -48,7 +48,7 @@ typedef struct mq_job {
 /* batch creation options; zero-initialised fields take the defaults */
 typedef struct mq_batch_opts {
     unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit, at most 2) */
-    unsigned lag;          /* pipeline lag between dependent stages, in job positions (0: 4) */
+    unsigned lag;          /* pipeline lag between dependent stages, in waves of the persistent grid (0: 2) */
     unsigned blas_chunk;   /* residues per BLAS work item (0: 16384); a multiple of 2048 */
     double wait_timeout_s; /* limit of every device-side wait (0: 2 s) */
     unsigned flags;        /* MQ_BATCH_* */

@@ -8,9 +8,11 @@
 //     (a per-polynomial counter of finished first-pass items);
 //   * the first items of a job with `after` wait for every item of that job (a per-job counter).
 // Items are ordered by a software-pipelining key: job chains (a job and the jobs that depend on
-// it) are numbered in submission order, and an item of stage s (its pass, plus the stages of the
-// jobs before it in its chain) of chain c gets the key c + s * lag, so a dependent stage trails
-// its producer by `lag` chains and its waits are normally already satisfied.
+// it) are laid out in submission order, chain c starting at position P(c) = the number of
+// first-stage items of the chains before it; an item of stage s (its pass, plus the stages of the
+// jobs before it in its chain) gets the key P(c) + s * D, D = lag x 4 x SMs items (lag waves of
+// the persistent grid, each CTA holding up to two items), so a dependent stage is fetched about
+// D items after its producer and its waits are normally already satisfied.
 // Deadlock freedom: an item waits only for items fetched before it; those were fetched by CTAs
 // that are running, whose own waits are again for earlier items, so every wait ends.  Each wait
 // is still bounded (globaltimer) and sets the batch status to MQ_ERR_TIMEOUT when it gives up;
@@ -153,11 +155,12 @@ __device__ __forceinline__ void run_blas(int op, const BlasArgs &b, unsigned lon
     }
 }
 
-constexpr int PT = 32;              // producer threads (one warp)
+constexpr int PT = 64;              // producer threads (two warps)
 constexpr int CT = BT + PT;         // threads per persistent CTA
 constexpr int BAR_COMPUTE = 1;      // named barrier of the BT compute threads
 constexpr int BAR_FULL = 2;         // + buffer: producer -> compute, "buffer b holds item k"
 constexpr int BAR_EMPTY = 4;        // + buffer: compute -> producer, "buffer b is free again"
+constexpr int BAR_PRODUCER = 6;     // named barrier of the PT producer threads
 
 // named barriers with immediate ids (a register id would make ptxas reserve all sixteen)
 __device__ __forceinline__ void bar_arrive(int id) {
@@ -173,7 +176,7 @@ __device__ __forceinline__ void bar_sync(int id) {
     else asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
 }
 
-// Stage an item's tiles with the producer warp: cp.async through L2 for 128-bit residues, batched
+// Stage an item's tiles with the producer warps: cp.async through L2 for 128-bit residues, batched
 // L2 loads for 64-bit residues (an 8-byte cp.async would allocate in the non-coherent L1).
 template <int W>
 __device__ __forceinline__ void stage_tiles(int L, const PassArgs &a, unsigned long long first, void *sm, int lane) {
@@ -211,7 +214,7 @@ __device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned
 // ctrs: [0] next item, [1] status, [2, 2 + njobs) per-job finished items, then per-polynomial
 // finished first-pass items of two-pass transforms.
 //
-// Warp-specialised: warp 8 is the producer.  For item k it waits until buffer k % 2 is free,
+// Warp-specialised: warps 8-9 are the producer.  For item k it waits until buffer k % 2 is free,
 // takes the next item index, waits (bounded) for the item's dependencies, copies its arguments
 // and stages its tiles into the buffer, and hands it over.  Warps 0-7 compute and store the item,
 // publish its completion on the counters, and free the buffer.  The producer therefore runs one
@@ -223,35 +226,41 @@ __global__ void __launch_bounds__(CT, 2)
     __shared__ PassArgs s_pa[2];
     __shared__ BlasArgs s_ba[2];
     __shared__ unsigned s_it[2];
+    __shared__ unsigned s_pit;
+    __shared__ int s_pok;
     const int tid = threadIdx.x;
     unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
 
-    if (tid >= BT) {  // ------------------------------------------------ producer warp
-        const int lane = tid - BT;
+    if (tid >= BT) {  // ----------------------------------------------- producer warps
+        const int lane = tid - BT;  // 0 .. PT-1
         for (unsigned k = 0;; ++k) {
             const int b = k & 1;
             if (k >= 2) bar_sync(BAR_EMPTY + b);
-            unsigned it = 0;
             if (lane == 0) {
-                it = atomicAdd(ctrs, 1u);
-                if (ld_status(status) != 0) it = n_items;  // the batch failed: drain
+                unsigned it0 = atomicAdd(ctrs, 1u);
+                if (ld_status(status) != 0) it0 = n_items;  // the batch failed: drain
+                int w = it0 < n_items;
+                if (w) {
+                    const ItemDev i0 = items[it0];
+                    const JobDev *J0 = jobs + i0.job;
+                    if (J0->kind == JK_NTT && J0->twopass && i0.pass == 1)
+                        w = wait_geq(poly_ctr + J0->poly_base + i0.poly, J0->groups0, status, limit_ns);
+                    else if (i0.pass == 0 && J0->after >= 0)
+                        w = wait_geq(job_ctr + J0->after, jobs[J0->after].n_items, status, limit_ns);
+                    if (!w) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
+                }
+                s_pit = it0;
+                s_pok = w;
             }
-            it = __shfl_sync(0xffffffffu, it, 0);
-            bool ok = it < n_items;
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");
+            const unsigned it = s_pit;
+            const bool ok = s_pok != 0;
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");  // s_pit reusable
             ItemDev item;
             const JobDev *J = jobs;
             if (ok) {
                 item = items[it];
                 J = jobs + item.job;
-                int w = 1;
-                if (lane == 0) {
-                    if (J->kind == JK_NTT && J->twopass && item.pass == 1)
-                        w = wait_geq(poly_ctr + J->poly_base + item.poly, J->groups0, status, limit_ns);
-                    else if (item.pass == 0 && J->after >= 0)
-                        w = wait_geq(job_ctr + J->after, jobs[J->after].n_items, status, limit_ns);
-                    if (!w) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
-                }
-                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             }
             if (!ok) {  // end of the work (or a failed wait): tell the compute warps and stop
                 if (lane == 0) s_it[b] = n_items;
@@ -511,7 +520,7 @@ static bool same_shape(const mq_job &a, const mq_job &b) {
 }
 
 static void defaults(mq_batch_opts &o) {
-    if (o.lag == 0) o.lag = 4;
+    if (o.lag == 0) o.lag = 2;
     if (o.blas_chunk == 0) o.blas_chunk = 16384;
     o.blas_chunk = (o.blas_chunk + 2047) / 2048 * 2048;
     if (o.wait_timeout_s <= 0) o.wait_timeout_s = 2.0;
@@ -589,6 +598,12 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
         }
     }
 
+    // pipeline lag in work items: `lag` waves of the persistent grid (2 CTAs per SM, each holding
+    // up to two items), so a dependent stage is fetched well after its producer items finished
+    int sms_for_lag = 0;
+    cudaDeviceGetAttribute(&sms_for_lag, cudaDevAttrMultiProcessorCount, b->device);
+    const unsigned long long lag_items = (unsigned long long)b->opts.lag * 4ull * (unsigned long long)(sms_for_lag > 0 ? sms_for_lag : 1);
+
     // expand into items, ordered by the pipelining key
     struct Key {
         unsigned long long key;
@@ -597,6 +612,8 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
     };
     std::vector<Key> keys;
     std::vector<unsigned> chain(njobs), depth(njobs);
+    std::vector<unsigned long long> chain_pos;  // first item position of each chain, in items
+    unsigned long long next_pos = 0;
     unsigned next_chain = 0, poly_ctrs = 0;
     bool dropped = !(b->opts.flags & MQ_BATCH_TEST_DROP_ITEM);
     long drop_job = -1;
@@ -606,6 +623,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
         if (j.after < 0) {
             chain[i] = next_chain++;
             depth[i] = 0;
+            chain_pos.push_back(next_pos);
         } else {
             chain[i] = chain[j.after];
             depth[i] = depth[j.after] + (unsigned)job_passes(jobs[j.after]);
@@ -615,7 +633,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             Key k;
             k.stage = depth[i] + pass;
             k.chain = chain[i];
-            k.key = (unsigned long long)k.chain + (unsigned long long)k.stage * b->opts.lag;
+            k.key = chain_pos[k.chain] + (unsigned long long)k.stage * lag_items;
             k.it.job = (unsigned)i;
             k.it.pass = pass;
             k.it.poly = poly;
@@ -655,6 +673,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             b->blas_items += chunks;
         }
         d.n_items = count;
+        if (j.after < 0) next_pos += count;  // chains are spaced by the items of their first job
         if (keys.size() > 0xffffffffull) {
             destroy_batch(b);
             return mq_fail(MQ_ERR_SIZE, "more than 2^32 work items");
@@ -904,7 +923,7 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
         has_deps |= jobs[i].after >= 0 || (is_ntt(jobs[i].kind) && jobs[i].plan && jobs[i].plan->log2n > LMAX);
     }
     const unsigned ctas[] = {1, 2};
-    const unsigned lags[] = {1, 2, 4, 8, 16};
+    const unsigned lags[] = {1, 2, 4, 8};
     const unsigned chunks[] = {8192, 16384, 65536};
     double best_ms = 1e30;
     mq_batch_opts bo{};
@@ -914,7 +933,7 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
     int rc = MQ_OK;
     for (unsigned c : ctas)
         for (unsigned l : lags) {
-            if (!has_deps && l != 4) continue;
+            if (!has_deps && l != 2) continue;
             for (unsigned ch : chunks) {
                 if (!has_blas && ch != 16384) continue;
                 mq_batch_opts o{};
