@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "../../include/mqntt_batch.h"
+#include "batch_internal.h"
 #include "blas_ops.cuh"
 #include "common.cuh"
 #include "hostmath.h"
@@ -50,32 +51,6 @@ using ntt_detail::Traits;
 
 constexpr int BT = 256;               // threads per persistent CTA
 constexpr int LMIN = 6, LMAX = 11;    // tile sizes the persistent kernel carries
-constexpr int JK_NTT = 0, JK_BLAS = 1;
-
-struct JobDev {
-    int kind;        // JK_NTT or JK_BLAS
-    int width;       // 1 or 2 words per residue
-    int inv;         // NTT direction
-    int op;          // BLAS op (OP_*)
-    int after;       // job this one waits for, or -1
-    int twopass;     // NTT: two passes (per-polynomial counters)
-    int L[2];        // NTT: tile log size of pass 0 and pass 1
-    unsigned n_items;     // items of this job (target of its completion counter)
-    unsigned poly_base;   // two-pass NTT: index of polynomial 0's counter
-    unsigned groups0;     // two-pass NTT: pass-0 items per polynomial
-    unsigned pad;
-    unsigned long long chunk;  // BLAS: residues per item
-    PassArgs pa[2];            // NTT passes
-    BlasArgs ba;               // BLAS operands
-};
-
-struct ItemDev {
-    unsigned job;
-    unsigned pass;
-    unsigned poly;
-    unsigned pad;
-    unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
-};
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -519,90 +494,47 @@ static bool same_shape(const mq_job &a, const mq_job &b) {
     return a.n == b.n && a.width == b.width;
 }
 
-static void defaults(mq_batch_opts &o) {
+void mq::batch_detail::apply_defaults(mq_batch_opts &o) {
     if (o.lag == 0) o.lag = 2;
     if (o.blas_chunk == 0) o.blas_chunk = 16384;
     o.blas_chunk = (o.blas_chunk + 2047) / 2048 * 2048;
     if (o.wait_timeout_s <= 0) o.wait_timeout_s = 2.0;
 }
 
-static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o);
-
-static void destroy_batch(mq_batch *b) {
-    if (!b) return;
-    cudaDeviceSynchronize();
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->cs) cudaStreamDestroy(b->cs);
-    if (b->done) cudaEventDestroy(b->done);
-    if (b->staged) cudaEventDestroy(b->staged);
-    if (b->h_status) cudaFreeHost(b->h_status);
-    if (b->pinned_jobs) cudaFreeHost(b->pinned_jobs);
-    if (b->djobs) cudaFree(b->djobs);
-    if (b->ditems) cudaFree(b->ditems);
-    if (b->dctrs) cudaFree(b->dctrs);
-    for (void *p : b->scratch)
-        if (p) cudaFree(p);
-    delete b;
+size_t mq::batch_detail::job_scratch_bytes(const mq_job &j) {
+    if (is_ntt(j.kind) && j.plan && j.plan->log2n > LMAX && j.plan->log2n <= 2 * LMAX && !(j.plan->flags & MQ_ORDER_BITREV))
+        return (j.batch ? j.batch : 1) * ((size_t)1 << j.plan->log2n) * 8u * (size_t)j.plan->width;
+    return 0;
 }
 
-static int enqueue_run(mq_batch *b, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b->dctrs, 0, b->n_ctrs * sizeof(unsigned), s);
-    if (e != cudaSuccess) return mq_cuda_fail(e, "counter reset");
-    persistent_kernel<<<b->grid, CT, 2 * b->smem, s>>>(b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs,
-                                                      (unsigned)b->hjobs.size(), b->limit_ns, b->smem);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
-    e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return mq_cuda_fail(e, "status copy");
+int mq::batch_detail::refill_jobs(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
+                                  std::vector<JobDev> &io) {
+    for (size_t i = 0; i < njobs; ++i) {
+        JobDev d;
+        int rc = fill_job(jobs[i], i, opts, scratch ? scratch[i] : nullptr, d);
+        if (rc) return rc;
+        d.n_items = io[i].n_items;  // counters and item bookkeeping stay those of the build
+        d.poly_base = io[i].poly_base;
+        d.groups0 = io[i].groups0;
+        io[i] = d;
+    }
     return MQ_OK;
 }
 
-extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs, const mq_batch_opts *opts, void *stream) {
-    if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!jobs || njobs == 0) return mq_fail(MQ_ERR_ARG, "a batch needs at least one job");
-    if (njobs > (1u << 24)) return mq_fail(MQ_ERR_ARG, "too many jobs");
-    mq_batch *b = new mq_batch();
-    cudaGetDevice(&b->device);
-    b->shape.assign(jobs, jobs + njobs);
-    if (opts) {
-        b->opts = *opts;
-    } else {
-        lookup_tuned(b->shape, b->opts);
-    }
-    defaults(b->opts);
-    b->limit_ns = (unsigned long long)(b->opts.wait_timeout_s * 1e9);
-    b->hjobs.resize(njobs);
-    b->scratch.assign(njobs, nullptr);
-
-    // staging for natural-order two-pass transforms
+int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
+                                   unsigned long long grid_items, BatchTables &out) {
+    out.jobs.assign(njobs, JobDev());
+    out.items.clear();
+    out.ntt_items = out.blas_items = 0;
     for (size_t i = 0; i < njobs; ++i) {
-        const mq_job &j = jobs[i];
-        if (is_ntt(j.kind) && j.plan && j.plan->log2n > LMAX && j.plan->log2n <= 2 * LMAX &&
-            !(j.plan->flags & MQ_ORDER_BITREV)) {
-            size_t bytes = (j.batch ? j.batch : 1) * ((size_t)1 << j.plan->log2n) * 8u * (size_t)j.plan->width;
-            cudaError_t e = cudaMalloc(&b->scratch[i], bytes);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                destroy_batch(b);
-                return mq_fail(MQ_ERR_OOM, "job %zu: staging of %zu bytes does not fit", i, bytes);
-            }
-        }
+        if (job_scratch_bytes(jobs[i]) && !(scratch && scratch[i]))
+            return mq_fail(MQ_ERR_ARG, "job %zu: natural-order transform without staging", i);
+        int rc = fill_job(jobs[i], i, opts, scratch ? scratch[i] : nullptr, out.jobs[i]);
+        if (rc) return rc;
     }
-    for (size_t i = 0; i < njobs; ++i) {
-        int rc = fill_job(jobs[i], i, b->opts, b->scratch[i], b->hjobs[i]);
-        if (rc) {
-            destroy_batch(b);
-            return rc;
-        }
-    }
-
-    // pipeline lag in work items: `lag` waves of the persistent grid (2 CTAs per SM, each holding
-    // up to two items), so a dependent stage is fetched well after its producer items finished
-    int sms_for_lag = 0;
-    cudaDeviceGetAttribute(&sms_for_lag, cudaDevAttrMultiProcessorCount, b->device);
-    const unsigned long long lag_items = (unsigned long long)b->opts.lag * 4ull * (unsigned long long)(sms_for_lag > 0 ? sms_for_lag : 1);
+    // pipeline lag in work items: `lag` times what the persistent grid holds at once, so a
+    // dependent stage is fetched well after its producer items finished
+    const unsigned long long lag_items = (unsigned long long)opts.lag * grid_items;
 
     // expand into items, ordered by the pipelining key
     struct Key {
@@ -615,11 +547,11 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
     std::vector<unsigned long long> chain_pos;  // first item position of each chain, in items
     unsigned long long next_pos = 0;
     unsigned next_chain = 0, poly_ctrs = 0;
-    bool dropped = !(b->opts.flags & MQ_BATCH_TEST_DROP_ITEM);
+    bool dropped = !(opts.flags & MQ_BATCH_TEST_DROP_ITEM);
     long drop_job = -1;
     for (size_t i = 0; i < njobs; ++i) {
         const mq_job &j = jobs[i];
-        JobDev &d = b->hjobs[i];
+        JobDev &d = out.jobs[i];
         if (j.after < 0) {
             chain[i] = next_chain++;
             depth[i] = 0;
@@ -652,7 +584,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             if (!d.twopass) {
                 const unsigned G = tiles_per_cta(d.L[0]);
                 for (unsigned long long t = 0; t < batch; t += G) push(0, 0, t);
-                b->ntt_items += (batch + G - 1) / G;
+                out.ntt_items += (batch + G - 1) / G;
             } else {
                 d.poly_base = poly_ctrs;
                 poly_ctrs += (unsigned)batch;
@@ -664,36 +596,133 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
                     if (pass == 0) d.groups0 = groups;
                     for (unsigned long long p = 0; p < batch; ++p)
                         for (unsigned g = 0; g < groups; ++g) push(pass, (unsigned)p, p * TP + (unsigned long long)g * G);
-                    b->ntt_items += batch * groups;
+                    out.ntt_items += batch * groups;
                 }
             }
         } else {
             const unsigned long long chunks = (d.ba.n + d.chunk - 1) / d.chunk;
             for (unsigned long long c = 0; c < chunks; ++c) push(0, 0, c);
-            b->blas_items += chunks;
+            out.blas_items += chunks;
         }
         d.n_items = count;
         if (j.after < 0) next_pos += count;  // chains are spaced by the items of their first job
-        if (keys.size() > 0xffffffffull) {
-            destroy_batch(b);
-            return mq_fail(MQ_ERR_SIZE, "more than 2^32 work items");
-        }
+        if (keys.size() > 0xffffffffull) return mq_fail(MQ_ERR_SIZE, "more than 2^32 work items");
     }
     // a dropped item still counts toward its job's target: nothing can complete that job
-    if (drop_job >= 0) b->hjobs[drop_job].n_items += 1;
+    if (drop_job >= 0) out.jobs[drop_job].n_items += 1;
     std::stable_sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) {
         if (x.key != y.key) return x.key < y.key;
         if (x.stage != y.stage) return x.stage < y.stage;
         return x.chain < y.chain;
     });
-    std::vector<ItemDev> items(keys.size());
-    for (size_t k = 0; k < keys.size(); ++k) items[k] = keys[k].it;
-    b->n_items = items.size();
-    b->n_ctrs = 2 + njobs + poly_ctrs;
+    out.items.resize(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) out.items[k] = keys[k].it;
+    out.n_ctrs = 2 + njobs + poly_ctrs;
+    return MQ_OK;
+}
+
+int mq::batch_detail::persistent_grid(unsigned ctas_per_sm, unsigned *grid, size_t *smem) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
+        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kernel_smem()));
+    });
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, CT, 2 * kernel_smem());
+    if (e != cudaSuccess || per_sm < 1) return mq_fail(MQ_ERR_CUDA, "the persistent kernel does not fit on an SM");
+    unsigned want = ctas_per_sm ? ctas_per_sm : 2;
+    *grid = (unsigned)sms * std::min<unsigned>(want, (unsigned)per_sm);
+    *smem = kernel_smem();
+    return MQ_OK;
+}
+
+cudaError_t mq::batch_detail::launch_persistent(const JobDev *djobs, const ItemDev *ditems, unsigned n_items,
+                                                unsigned *dctrs, size_t n_ctrs, unsigned njobs,
+                                                unsigned long long limit_ns, unsigned grid, size_t smem,
+                                                cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(dctrs, 0, n_ctrs * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    persistent_kernel<<<grid, CT, 2 * smem, s>>>(djobs, ditems, n_items, dctrs, njobs, limit_ns, smem);
+    return cudaGetLastError();
+}
+
+static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o);
+
+static void destroy_batch(mq_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->pinned_jobs) cudaFreeHost(b->pinned_jobs);
+    if (b->djobs) cudaFree(b->djobs);
+    if (b->ditems) cudaFree(b->ditems);
+    if (b->dctrs) cudaFree(b->dctrs);
+    for (void *p : b->scratch)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+static int enqueue_run(mq_batch *b, cudaStream_t s) {
+    cudaError_t e = launch_persistent(b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
+                                      (unsigned)b->hjobs.size(), b->limit_ns, b->grid, b->smem, s);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
+    e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "status copy");
+    return MQ_OK;
+}
+
+extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs, const mq_batch_opts *opts, void *stream) {
+    if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!jobs || njobs == 0) return mq_fail(MQ_ERR_ARG, "a batch needs at least one job");
+    if (njobs > (1u << 24)) return mq_fail(MQ_ERR_ARG, "too many jobs");
+    mq_batch *b = new mq_batch();
+    cudaGetDevice(&b->device);
+    b->shape.assign(jobs, jobs + njobs);
+    if (opts) {
+        b->opts = *opts;
+    } else {
+        lookup_tuned(b->shape, b->opts);
+    }
+    apply_defaults(b->opts);
+    b->limit_ns = (unsigned long long)(b->opts.wait_timeout_s * 1e9);
+    b->scratch.assign(njobs, nullptr);
+    int rc = persistent_grid(b->opts.ctas_per_sm, &b->grid, &b->smem);
+    if (rc) {
+        destroy_batch(b);
+        return rc;
+    }
+    // staging for natural-order two-pass transforms
+    for (size_t i = 0; i < njobs; ++i) {
+        const size_t bytes = job_scratch_bytes(jobs[i]);
+        if (!bytes) continue;
+        cudaError_t e = cudaMalloc(&b->scratch[i], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            destroy_batch(b);
+            return mq_fail(MQ_ERR_OOM, "job %zu: staging of %zu bytes does not fit", i, bytes);
+        }
+    }
+    BatchTables t;
+    rc = build_tables(jobs, njobs, b->opts, b->scratch.data(), 2ull * b->grid, t);
+    if (rc) {
+        destroy_batch(b);
+        return rc;
+    }
+    b->hjobs = std::move(t.jobs);
+    b->n_items = t.items.size();
+    b->n_ctrs = t.n_ctrs;
+    b->ntt_items = t.ntt_items;
+    b->blas_items = t.blas_items;
 
     cudaError_t e;
     if ((e = cudaMalloc(&b->djobs, njobs * sizeof(JobDev))) != cudaSuccess ||
-        (e = cudaMalloc(&b->ditems, std::max<size_t>(1, items.size()) * sizeof(ItemDev))) != cudaSuccess ||
+        (e = cudaMalloc(&b->ditems, std::max<size_t>(1, t.items.size()) * sizeof(ItemDev))) != cudaSuccess ||
         (e = cudaMalloc(&b->dctrs, b->n_ctrs * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMallocHost(&b->pinned_jobs, njobs * sizeof(JobDev))) != cudaSuccess ||
         (e = cudaMallocHost(&b->h_status, sizeof(int))) != cudaSuccess) {
@@ -705,28 +734,12 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
     cudaStream_t s = (cudaStream_t)stream;
     memcpy(b->pinned_jobs, b->hjobs.data(), njobs * sizeof(JobDev));
     if ((e = cudaMemcpyAsync(b->djobs, b->pinned_jobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b->ditems, items.data(), items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->ditems, t.items.data(), t.items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
         destroy_batch(b);
         return mq_cuda_fail(e, "batch table upload");
     }
-
-    // one wave of persistent CTAs
-    b->smem = kernel_smem();
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kernel_smem()));
-    });
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, CT, 2 * b->smem);
-    if (e != cudaSuccess || per_sm < 1) {
-        destroy_batch(b);
-        return mq_fail(MQ_ERR_CUDA, "the persistent kernel does not fit on an SM");
-    }
-    unsigned want = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
-    b->grid = (unsigned)sms * std::min<unsigned>(want, (unsigned)per_sm);
-
     if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess) {
@@ -738,7 +751,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             destroy_batch(b);
             return mq_cuda_fail(e, "graph capture");
         }
-        int rc = enqueue_run(b, b->cs);
+        rc = enqueue_run(b, b->cs);
         cudaError_t e2 = cudaStreamEndCapture(b->cs, &b->graph);
         if (rc || e2 != cudaSuccess) {
             destroy_batch(b);
@@ -758,15 +771,9 @@ extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, vo
     if (njobs != b->shape.size()) return mq_fail(MQ_ERR_ARG, "the batch has %zu jobs, got %zu", b->shape.size(), njobs);
     for (size_t i = 0; i < njobs; ++i)
         if (!same_shape(b->shape[i], jobs[i])) return mq_fail(MQ_ERR_ARG, "job %zu differs in shape from the batch's", i);
-    std::vector<JobDev> next(njobs);
-    for (size_t i = 0; i < njobs; ++i) {
-        int rc = fill_job(jobs[i], i, b->opts, b->scratch[i], next[i]);
-        if (rc) return rc;
-        // counters and item bookkeeping stay those of the creation
-        next[i].n_items = b->hjobs[i].n_items;
-        next[i].poly_base = b->hjobs[i].poly_base;
-        next[i].groups0 = b->hjobs[i].groups0;
-    }
+    std::vector<JobDev> next = b->hjobs;
+    int rc = refill_jobs(jobs, njobs, b->opts, b->scratch.data(), next);
+    if (rc) return rc;
     cudaError_t e = cudaEventSynchronize(b->staged);  // the previous upload has left the staging buffer
     if (e != cudaSuccess) return mq_cuda_fail(e, "staging wait");
     b->hjobs = next;
@@ -963,7 +970,7 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
             }
         }
     *best = bo;
-    defaults(*best);
+    apply_defaults(*best);
     if (cache_path && *cache_path) cache_put(cache_path, shape_key(std::vector<mq_job>(jobs, jobs + njobs)), *best, best_ms);
 done:
     cudaEventDestroy(t0);

@@ -1,0 +1,74 @@
+// batch_internal.h -- the batched persistent form's tables and launcher, shared by the batch API
+// (batch.cu) and the serving loop (serve.cu).  Internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/mqntt_batch.h"
+#include "common.cuh"
+
+namespace mq {
+namespace batch_detail {
+
+constexpr int JK_NTT = 0, JK_BLAS = 1;
+
+struct JobDev {
+    int kind;        // JK_NTT or JK_BLAS
+    int width;       // 1 or 2 words per residue
+    int inv;         // NTT direction
+    int op;          // BLAS op (OP_*)
+    int after;       // job this one waits for, or -1
+    int twopass;     // NTT: two passes (per-polynomial counters)
+    int L[2];        // NTT: tile log size of pass 0 and pass 1
+    unsigned n_items;     // items of this job (target of its completion counter)
+    unsigned poly_base;   // two-pass NTT: index of polynomial 0's counter
+    unsigned groups0;     // two-pass NTT: pass-0 items per polynomial
+    unsigned pad;
+    unsigned long long chunk;  // BLAS: residues per item
+    PassArgs pa[2];            // NTT passes
+    BlasArgs ba;               // BLAS operands
+};
+
+struct ItemDev {
+    unsigned job;
+    unsigned pass;
+    unsigned poly;
+    unsigned pad;
+    unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
+};
+
+// Host-side expansion of a job list into the device tables of one launch.
+struct BatchTables {
+    std::vector<JobDev> jobs;
+    std::vector<ItemDev> items;
+    size_t n_ctrs = 0;        // counters to zero before each launch
+    size_t ntt_items = 0, blas_items = 0;
+};
+
+// Staging bytes a job needs (natural-order transforms in two passes), 0 if none.
+size_t job_scratch_bytes(const mq_job &j);
+
+// Validate `jobs`, fill `out` (job descriptors with `scratch[i]` as job i's staging, and the work
+// items in pipelining order).  `grid_items` is the number of items the persistent grid holds at
+// once (it scales the pipelining lag).  Returns MQ_OK or an MQ_ERR_* code (message set).
+int build_tables(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
+                 unsigned long long grid_items, BatchTables &out);
+
+// Re-fill the descriptors of an already built batch with new pointers / scalars (same shapes).
+int refill_jobs(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
+                std::vector<JobDev> &jobs_io);
+
+// Persistent CTAs for `ctas_per_sm` (0: as many as fit, at most 2) on the current device, and the
+// dynamic shared memory of a launch.
+int persistent_grid(unsigned ctas_per_sm, unsigned *grid, size_t *smem);
+
+// Zero the counters and launch the persistent kernel on `s` (asynchronous).
+cudaError_t launch_persistent(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, unsigned *dctrs,
+                              size_t n_ctrs, unsigned njobs, unsigned long long limit_ns, unsigned grid, size_t smem,
+                              cudaStream_t s);
+
+void apply_defaults(mq_batch_opts &o);
+
+}  // namespace batch_detail
+}  // namespace mq

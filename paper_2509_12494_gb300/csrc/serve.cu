@@ -1,0 +1,535 @@
+// serve.cu -- the continuous-batching request loop (include/mqntt_serve.h).
+//
+// One server thread owns the pending queue and `slots` in-flight batches, each with its own
+// stream and preallocated device / pinned tables.  Whenever a slot is free it takes the pending
+// requests in arrival order while the memory budget allows, expands them into work items
+// (build_tables of the batched form), uploads the tables and launches the persistent kernel on the
+// slot's stream, followed by a host callback that stamps the completion time.  Natural-order
+// transforms above 2^12 get their staging from the library's stream-ordered pool on that stream.
+// The plain mode runs each request as its own per-call launch instead, on one stream, with one
+// callback per request: the same arrivals through the per-call path, for comparison.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/mqntt_serve.h"
+#include "batch_internal.h"
+#include "plan.h"
+
+int mq_fail(int code, const char *fmt, ...);
+int mq_cuda_fail(cudaError_t e, const char *where);
+int mq_pool_alloc(void **p, size_t bytes, cudaStream_t s);
+int mq_pool_free(void *p, cudaStream_t s);
+
+using namespace mq::batch_detail;
+
+static uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+static bool is_ntt_kind(int k) { return k == MQ_JOB_NTT_FORWARD || k == MQ_JOB_NTT_INVERSE; }
+
+namespace {
+
+struct Ticket {
+    mq_job job;
+    uint64_t t_submit = 0, t_done = 0;
+    size_t bytes = 0;
+    double butterflies = 0, modmuls = 0;
+    int status = MQ_OK;
+    bool done = false;
+};
+
+struct Server;
+
+struct Slot {
+    Server *srv = nullptr;
+    cudaStream_t stream = nullptr;
+    JobDev *djobs = nullptr, *hjobs = nullptr;
+    ItemDev *ditems = nullptr, *hitems = nullptr;
+    unsigned *dctrs = nullptr;
+    int *h_status = nullptr;
+    size_t cap_jobs = 0, cap_items = 0, cap_ctrs = 0;
+    std::vector<uint64_t> tickets;
+    std::atomic<bool> busy{false}, finished{false};
+    std::atomic<uint64_t> t_done{0};
+};
+
+struct PlainDone {
+    Server *srv;
+    uint64_t id;
+};
+
+}  // namespace
+
+struct mq_server {
+    Server *impl;
+};
+
+namespace {
+
+struct Server {
+    mq_server_cfg cfg{};
+    mq_batch_opts opts{};
+    int device = 0;
+    unsigned grid = 0;
+    size_t smem = 0;
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the server thread
+    std::condition_variable done_cv;  // wakes waiters
+    std::deque<uint64_t> pending;
+    std::deque<Ticket> tickets;       // ticket id = index + 1
+    size_t inflight = 0, peak = 0;
+    std::vector<Slot *> slots;
+    cudaStream_t plain_stream = nullptr;
+    std::atomic<uint64_t> plain_outstanding{0};
+    std::thread th;
+    bool stop = false;
+    // statistics since the last reset
+    std::vector<double> lat_ms;
+    uint64_t completed = 0, failed = 0, batches = 0, batch_jobs = 0;
+    uint64_t t_first = 0, t_last = 0;
+    double bfly = 0, mm = 0;
+    int thread_error = MQ_OK;
+
+    Ticket &ticket(uint64_t id) { return tickets[id - 1]; }
+
+    void finish(uint64_t id, int status, uint64_t t_done) {  // under mu
+        Ticket &t = ticket(id);
+        t.done = true;
+        t.status = status;
+        t.t_done = t_done;
+        inflight -= t.bytes;
+        if (status == MQ_OK) {
+            ++completed;
+            bfly += t.butterflies;
+            mm += t.modmuls;
+        } else {
+            ++failed;
+        }
+        lat_ms.push_back((double)(t_done - t.t_submit) * 1e-6);
+        if (t_done > t_last) t_last = t_done;
+    }
+};
+
+void CUDART_CB slot_done_cb(void *arg) {
+    Slot *sl = static_cast<Slot *>(arg);
+    sl->t_done.store(now_ns());
+    sl->finished.store(true);
+    {
+        std::lock_guard<std::mutex> lk(sl->srv->mu);
+    }
+    sl->srv->cv.notify_all();
+}
+
+void CUDART_CB plain_done_cb(void *arg) {
+    PlainDone *p = static_cast<PlainDone *>(arg);
+    Server *s = p->srv;
+    const uint64_t t = now_ns();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->finish(p->id, MQ_OK, t);
+        s->plain_outstanding.fetch_sub(1);
+    }
+    s->done_cv.notify_all();
+    s->cv.notify_all();
+    delete p;
+}
+
+size_t job_bytes(const mq_job &j) {
+    if (is_ntt_kind(j.kind)) {
+        size_t op = (j.batch ? j.batch : 1) * ((size_t)1 << j.plan->log2n) * 8u * (size_t)j.plan->width;
+        return op + job_scratch_bytes(j);
+    }
+    return (j.kind == MQ_JOB_AXPY ? 2u : 3u) * j.n * 8u * (size_t)j.width;
+}
+
+void job_work(const mq_job &j, double *bfly, double *mm) {
+    if (is_ntt_kind(j.kind)) {
+        double b = (double)(j.batch ? j.batch : 1) * (double)((size_t)1 << (j.plan->log2n - 1)) * j.plan->log2n;
+        *bfly = b;
+        *mm = b;
+    } else {
+        *bfly = 0;
+        *mm = (j.kind == MQ_JOB_VMUL || j.kind == MQ_JOB_AXPY) ? (double)j.n : 0.0;
+    }
+}
+
+int grow(Slot *sl, size_t njobs, size_t nitems, size_t nctrs) {
+    cudaError_t e = cudaSuccess;
+    if (njobs > sl->cap_jobs) {
+        size_t cap = std::max(njobs, 2 * sl->cap_jobs);
+        if (sl->djobs) cudaFree(sl->djobs);
+        if (sl->hjobs) cudaFreeHost(sl->hjobs);
+        sl->djobs = nullptr;
+        sl->hjobs = nullptr;
+        if ((e = cudaMalloc(&sl->djobs, cap * sizeof(JobDev))) != cudaSuccess ||
+            (e = cudaMallocHost(&sl->hjobs, cap * sizeof(JobDev))) != cudaSuccess)
+            return mq_fail(MQ_ERR_OOM, "server tables do not fit");
+        sl->cap_jobs = cap;
+    }
+    if (nitems > sl->cap_items) {
+        size_t cap = std::max(nitems, 2 * sl->cap_items);
+        if (sl->ditems) cudaFree(sl->ditems);
+        if (sl->hitems) cudaFreeHost(sl->hitems);
+        sl->ditems = nullptr;
+        sl->hitems = nullptr;
+        if ((e = cudaMalloc(&sl->ditems, cap * sizeof(ItemDev))) != cudaSuccess ||
+            (e = cudaMallocHost(&sl->hitems, cap * sizeof(ItemDev))) != cudaSuccess)
+            return mq_fail(MQ_ERR_OOM, "server tables do not fit");
+        sl->cap_items = cap;
+    }
+    if (nctrs > sl->cap_ctrs) {
+        size_t cap = std::max(nctrs, 2 * sl->cap_ctrs);
+        if (sl->dctrs) cudaFree(sl->dctrs);
+        sl->dctrs = nullptr;
+        if ((e = cudaMalloc(&sl->dctrs, cap * sizeof(unsigned))) != cudaSuccess)
+            return mq_fail(MQ_ERR_OOM, "server counters do not fit");
+        sl->cap_ctrs = cap;
+    }
+    return MQ_OK;
+}
+
+// Build and launch one batch of requests on a free slot (called without the server lock).
+int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
+    const size_t n = jobs.size();
+    std::vector<void *> scratch(n, nullptr);
+    int rc = MQ_OK;
+    for (size_t i = 0; i < n && !rc; ++i) {
+        size_t b = job_scratch_bytes(jobs[i]);
+        if (b) rc = mq_pool_alloc(&scratch[i], b, sl->stream);
+    }
+    BatchTables t;
+    if (!rc) rc = build_tables(jobs.data(), n, s->opts, scratch.data(), 2ull * s->grid, t);
+    if (!rc) rc = grow(sl, n, std::max<size_t>(1, t.items.size()), t.n_ctrs);
+    if (!rc) {
+        memcpy(sl->hjobs, t.jobs.data(), n * sizeof(JobDev));
+        memcpy(sl->hitems, t.items.data(), t.items.size() * sizeof(ItemDev));
+        *sl->h_status = 0;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(sl->djobs, sl->hjobs, n * sizeof(JobDev), cudaMemcpyHostToDevice, sl->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(sl->ditems, sl->hitems, t.items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice,
+                                 sl->stream)) != cudaSuccess ||
+            (e = launch_persistent(sl->djobs, sl->ditems, (unsigned)t.items.size(), sl->dctrs, t.n_ctrs, (unsigned)n,
+                                   (unsigned long long)(s->opts.wait_timeout_s * 1e9), s->grid, s->smem,
+                                   sl->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(sl->h_status, sl->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, sl->stream)) !=
+                cudaSuccess)
+            rc = mq_cuda_fail(e, "server batch launch");
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (scratch[i]) mq_pool_free(scratch[i], sl->stream);  // stream-ordered after the kernel
+    if (!rc) {
+        cudaError_t e = cudaLaunchHostFunc(sl->stream, slot_done_cb, sl);
+        if (e != cudaSuccess) rc = mq_cuda_fail(e, "server completion callback");
+    }
+    return rc;
+}
+
+int run_plain(Server *s, uint64_t id) {
+    const mq_job &j = s->ticket(id).job;
+    void *st = (void *)s->plain_stream;
+    int rc;
+    switch (j.kind) {
+    case MQ_JOB_NTT_FORWARD: rc = ntt_forward(j.plan, j.data, j.batch ? j.batch : 1, j.stride, st); break;
+    case MQ_JOB_NTT_INVERSE: rc = ntt_inverse(j.plan, j.data, j.batch ? j.batch : 1, j.stride, st); break;
+    case MQ_JOB_VADD: rc = mod_vadd(j.data, j.a, j.b, j.n, j.q, j.width, st); break;
+    case MQ_JOB_VSUB: rc = mod_vsub(j.data, j.a, j.b, j.n, j.q, j.width, st); break;
+    case MQ_JOB_VMUL: rc = mod_vmul(j.data, j.a, j.b, j.n, j.q, j.width, st); break;
+    default: rc = mod_axpy(j.data, j.scalar, j.a, j.n, j.q, j.width, st); break;
+    }
+    if (rc) return rc;
+    PlainDone *p = new PlainDone{s, id};
+    cudaError_t e = cudaLaunchHostFunc(s->plain_stream, plain_done_cb, p);
+    if (e != cudaSuccess) {
+        delete p;
+        return mq_cuda_fail(e, "plain completion callback");
+    }
+    return MQ_OK;
+}
+
+void server_loop(Server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        // completions of batches
+        for (Slot *sl : s->slots) {
+            if (sl->busy.load() && sl->finished.load()) {
+                const int st = *(volatile int *)sl->h_status;
+                const uint64_t t = sl->t_done.load();
+                for (uint64_t id : sl->tickets) s->finish(id, st, t);
+                sl->tickets.clear();
+                sl->finished.store(false);
+                sl->busy.store(false);
+                s->done_cv.notify_all();
+            }
+        }
+        bool any_busy = false;
+        for (Slot *sl : s->slots) any_busy |= sl->busy.load();
+        if (s->stop && s->pending.empty() && !any_busy && s->plain_outstanding.load() == 0) break;
+
+        // dispatch
+        if (s->cfg.mode == MQ_SERVE_PLAIN) {
+            while (!s->pending.empty()) {
+                const uint64_t id = s->pending.front();
+                Ticket &t = s->ticket(id);
+                if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes && s->plain_outstanding.load() > 0) break;
+                s->pending.pop_front();
+                s->inflight += t.bytes;
+                s->peak = std::max(s->peak, s->inflight);
+                s->plain_outstanding.fetch_add(1);
+                ++s->batches;
+                ++s->batch_jobs;
+                lk.unlock();
+                int rc = run_plain(s, id);
+                lk.lock();
+                if (rc) {
+                    s->finish(id, rc, now_ns());
+                    s->plain_outstanding.fetch_sub(1);
+                    s->done_cv.notify_all();
+                }
+            }
+        } else {
+            for (Slot *sl : s->slots) {
+                if (sl->busy.load() || s->pending.empty()) continue;
+                if (s->cfg.linger_us > 0 && s->pending.size() < s->cfg.max_batch_jobs) {
+                    const uint64_t age = now_ns() - s->ticket(s->pending.front()).t_submit;
+                    if ((double)age < s->cfg.linger_us * 1e3 && any_busy) break;
+                }
+                std::vector<mq_job> jobs;
+                while (!s->pending.empty() && jobs.size() < s->cfg.max_batch_jobs) {
+                    Ticket &t = s->ticket(s->pending.front());
+                    if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes) break;  // wait for memory to free up
+                    s->inflight += t.bytes;
+                    jobs.push_back(t.job);
+                    sl->tickets.push_back(s->pending.front());
+                    s->pending.pop_front();
+                }
+                if (jobs.empty()) break;
+                s->peak = std::max(s->peak, s->inflight);
+                sl->busy.store(true);
+                ++s->batches;
+                s->batch_jobs += jobs.size();
+                lk.unlock();
+                int rc = launch_batch(s, sl, jobs);
+                lk.lock();
+                if (rc) {
+                    const uint64_t t = now_ns();
+                    for (uint64_t id : sl->tickets) s->finish(id, rc, t);
+                    sl->tickets.clear();
+                    sl->busy.store(false);
+                    s->done_cv.notify_all();
+                }
+                any_busy = true;
+            }
+        }
+        s->cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+
+extern "C" int mq_server_create(mq_server **out, const mq_server_cfg *cfg) {
+    if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    Server *s = new Server();
+    if (cfg) s->cfg = *cfg;
+    if (s->cfg.mode != MQ_SERVE_BATCHED && s->cfg.mode != MQ_SERVE_PLAIN) {
+        delete s;
+        return mq_fail(MQ_ERR_ARG, "unknown server mode %d", s->cfg.mode);
+    }
+    cudaGetDevice(&s->device);
+    if (s->cfg.hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        s->cfg.hbm_budget_bytes = fr / 2;
+    }
+    if (s->cfg.slots == 0) s->cfg.slots = 2;
+    if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 4096;
+    if (s->cfg.wait_timeout_s <= 0) s->cfg.wait_timeout_s = 2.0;
+    s->opts.wait_timeout_s = s->cfg.wait_timeout_s;
+    apply_defaults(s->opts);
+    int rc = persistent_grid(0, &s->grid, &s->smem);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&s->plain_stream, cudaStreamNonBlocking);
+    for (unsigned i = 0; i < s->cfg.slots && e == cudaSuccess; ++i) {
+        Slot *sl = new Slot();
+        sl->srv = s;
+        s->slots.push_back(sl);
+        if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+        e = cudaMallocHost(&sl->h_status, sizeof(int));
+    }
+    if (e != cudaSuccess) {
+        mq_server tmp{s};
+        mq_server_destroy(new mq_server(tmp));
+        return mq_cuda_fail(e, "server streams");
+    }
+    s->th = std::thread(server_loop, s);
+    *out = new mq_server{s};
+    return MQ_OK;
+}
+
+extern "C" int mq_submit(mq_server *srv, const mq_job *job, uint64_t *ticket) {
+    if (!srv || !job || !ticket) return mq_fail(MQ_ERR_ARG, "NULL argument");
+    Server *s = srv->impl;
+    if (job->after != -1) return mq_fail(MQ_ERR_ARG, "served jobs are independent: `after` must be -1");
+    if (is_ntt_kind(job->kind) && !job->plan) return mq_fail(MQ_ERR_ARG, "NTT job without a plan");
+    // full validation through the batch table builder (with a stand-in staging pointer)
+    {
+        mq_job j = *job;
+        BatchTables t;
+        void *dummy = (void *)(uintptr_t)256;
+        int rc = build_tables(&j, 1, s->opts, &dummy, 1, t);
+        if (rc) return rc;
+    }
+    Ticket t;
+    t.job = *job;
+    t.bytes = job_bytes(*job);
+    job_work(*job, &t.butterflies, &t.modmuls);
+    if (t.bytes > s->cfg.hbm_budget_bytes)
+        return mq_fail(MQ_ERR_SIZE, "the job needs %zu bytes, more than the server's whole budget (%zu)", t.bytes,
+                       s->cfg.hbm_budget_bytes);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        t.t_submit = now_ns();
+        if (s->t_first == 0) s->t_first = t.t_submit;
+        s->tickets.push_back(t);
+        *ticket = s->tickets.size();
+        s->pending.push_back(*ticket);
+    }
+    s->cv.notify_all();
+    return MQ_OK;
+}
+
+extern "C" int mq_poll(mq_server *srv, uint64_t ticket, int *done, int *status) {
+    if (!srv || !done) return mq_fail(MQ_ERR_ARG, "NULL argument");
+    Server *s = srv->impl;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticket == 0 || ticket > s->tickets.size()) return mq_fail(MQ_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    const Ticket &t = s->ticket(ticket);
+    *done = t.done;
+    if (status) *status = t.done ? t.status : MQ_OK;
+    return MQ_OK;
+}
+
+extern "C" int mq_wait(mq_server *srv, uint64_t ticket, double timeout_s, int *status) {
+    if (!srv) return mq_fail(MQ_ERR_ARG, "NULL server");
+    Server *s = srv->impl;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (ticket == 0 || ticket > s->tickets.size()) return mq_fail(MQ_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (!s->ticket(ticket).done) {
+        if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !s->ticket(ticket).done)
+            return mq_fail(MQ_ERR_TIMEOUT, "ticket %llu not done after %.3f s", (unsigned long long)ticket, timeout_s);
+    }
+    if (status) *status = s->ticket(ticket).status;
+    return MQ_OK;
+}
+
+extern "C" int mq_server_drain(mq_server *srv, double timeout_s) {
+    if (!srv) return mq_fail(MQ_ERR_ARG, "NULL server");
+    Server *s = srv->impl;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        bool all = true;
+        for (const Ticket &t : s->tickets) all &= t.done;
+        if (all) return MQ_OK;
+        if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+            bool all2 = true;
+            for (const Ticket &t : s->tickets) all2 &= t.done;
+            return all2 ? MQ_OK : mq_fail(MQ_ERR_TIMEOUT, "server not drained after %.3f s", timeout_s);
+        }
+    }
+}
+
+extern "C" int mq_server_stats(mq_server *srv, mq_stats *out) {
+    if (!srv || !out) return mq_fail(MQ_ERR_ARG, "NULL argument");
+    Server *s = srv->impl;
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof *out);
+    out->submitted = s->tickets.size();
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->batches = s->batches;
+    out->peak_inflight_bytes = s->peak;
+    out->mean_batch_jobs = s->batches ? (double)s->batch_jobs / (double)s->batches : 0.0;
+    std::vector<double> v = s->lat_ms;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) {
+            size_t k = (size_t)std::min<double>((double)(v.size() - 1), std::max(0.0, p * (double)v.size() - 1.0 + 0.5));
+            return v[k];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = v.back();
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_ms = sum / (double)v.size();
+    }
+    if (s->t_last > s->t_first) {
+        out->span_s = (double)(s->t_last - s->t_first) * 1e-9;
+        out->jobs_per_s = (double)s->completed / out->span_s;
+        out->butterflies_per_s = s->bfly / out->span_s;
+        out->modmul_per_s = s->mm / out->span_s;
+    }
+    return MQ_OK;
+}
+
+extern "C" int mq_server_reset_stats(mq_server *srv) {
+    if (!srv) return mq_fail(MQ_ERR_ARG, "NULL server");
+    Server *s = srv->impl;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_ms.clear();
+    s->completed = s->failed = s->batches = s->batch_jobs = 0;
+    s->t_first = s->t_last = 0;
+    s->bfly = s->mm = 0;
+    s->peak = s->inflight;
+    return MQ_OK;
+}
+
+extern "C" int mq_server_destroy(mq_server *srv) {
+    if (!srv) return MQ_OK;
+    Server *s = srv->impl;
+    if (s->th.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv.notify_all();
+        s->th.join();
+    }
+    cudaDeviceSynchronize();
+    for (Slot *sl : s->slots) {
+        if (sl->stream) cudaStreamDestroy(sl->stream);
+        if (sl->djobs) cudaFree(sl->djobs);
+        if (sl->ditems) cudaFree(sl->ditems);
+        if (sl->dctrs) cudaFree(sl->dctrs);
+        if (sl->hjobs) cudaFreeHost(sl->hjobs);
+        if (sl->hitems) cudaFreeHost(sl->hitems);
+        if (sl->h_status) cudaFreeHost(sl->h_status);
+        delete sl;
+    }
+    if (s->plain_stream) cudaStreamDestroy(s->plain_stream);
+    delete s;
+    delete srv;
+    return MQ_OK;
+}

@@ -72,6 +72,14 @@ def load(build_if_missing: bool = False):
                           ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
         "mq_batch_destroy": [_vp],
         "mq_autotune_batch": [_vp, ctypes.c_size_t, _vp, ctypes.c_char_p, _vp],
+        "mq_server_create": [ctypes.POINTER(_vp), _vp],
+        "mq_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
+        "mq_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "mq_wait": [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)],
+        "mq_server_drain": [_vp, ctypes.c_double],
+        "mq_server_stats": [_vp, _vp],
+        "mq_server_reset_stats": [_vp],
+        "mq_server_destroy": [_vp],
         "mq_last_error": [],
         "mq_version": [],
     }
@@ -289,6 +297,84 @@ def mq_autotune_batch(jobs, cache_path: str | None = None, stream=None) -> mq_ba
     _check(load().mq_autotune_batch(ctypes.cast(arr, _vp), len(jobs), ctypes.byref(best),
                                     cache_path.encode() if cache_path else None, stream_handle(stream)))
     return best
+
+
+# ------------------------------------------------------------------------- serving (mqntt_serve.h)
+
+MQ_SERVE_BATCHED, MQ_SERVE_PLAIN = 0, 1
+
+
+class mq_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("slots", ctypes.c_uint), ("max_batch_jobs", ctypes.c_uint),
+                ("linger_us", ctypes.c_double), ("wait_timeout_s", ctypes.c_double), ("mode", ctypes.c_int)]
+
+
+class mq_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("jobs_per_s", ctypes.c_double), ("butterflies_per_s", ctypes.c_double),
+                ("modmul_per_s", ctypes.c_double), ("mean_batch_jobs", ctypes.c_double),
+                ("peak_inflight_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """Owns an mq_server* (freed by mq_server_destroy or on garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mq_server_destroy(self.handle)
+            self.handle = None
+
+
+def mq_server_create(cfg: mq_server_cfg | None = None) -> Server:
+    h = _vp()
+    _check(load().mq_server_create(ctypes.byref(h), ctypes.cast(ctypes.byref(cfg), _vp) if cfg is not None else None))
+    return Server(h.value)
+
+
+def mq_submit(server: Server, job: mq_job) -> int:
+    t = ctypes.c_uint64()
+    _check(load().mq_submit(server.handle, ctypes.cast(ctypes.byref(job), _vp), ctypes.byref(t)))
+    return t.value
+
+
+def mq_poll(server: Server, ticket: int):
+    done, st = ctypes.c_int(), ctypes.c_int()
+    _check(load().mq_poll(server.handle, ticket, ctypes.byref(done), ctypes.byref(st)))
+    return bool(done.value), st.value
+
+
+def mq_wait(server: Server, ticket: int, timeout_s: float = 60.0) -> int:
+    st = ctypes.c_int()
+    _check(load().mq_wait(server.handle, ticket, timeout_s, ctypes.byref(st)))
+    return st.value
+
+
+def mq_server_drain(server: Server, timeout_s: float = 120.0):
+    _check(load().mq_server_drain(server.handle, timeout_s))
+
+
+def mq_server_stats(server: Server) -> dict:
+    st = mq_stats()
+    _check(load().mq_server_stats(server.handle, ctypes.cast(ctypes.byref(st), _vp)))
+    return st.as_dict()
+
+
+def mq_server_reset_stats(server: Server):
+    _check(load().mq_server_reset_stats(server.handle))
+
+
+def mq_server_destroy(server: Server):
+    if server.handle:
+        _check(load().mq_server_destroy(server.handle))
+        server.handle = None
 
 
 # ------------------------------------------------------------------------- tensor marshalling
