@@ -49,6 +49,11 @@ def parse():
     p.add_argument("--no-blas", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--workload", default="uniform", choices=["uniform", "serve"],
+                   help="uniform: the default line (uniform batch, plus BLAS and the uneven batch as extra blocks); "
+                        "serve: the Poisson serving sweep")
+    p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=1.5)
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
     return p.parse_args()
@@ -322,6 +327,8 @@ def run_gpu(args, rank, world):
 
     if not args.no_blas:
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
+    if not args.no_uneven:
+        out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps)
 
     out["clocks"] = clocks
     return out
@@ -364,6 +371,193 @@ def bench_blas(M, torch, dev, stream, flush):
             res[f"{op}_{bits}"] = entry
         del a, b, c
     return res
+
+
+# ----------------------------------------------------------------------------------- uneven batch
+
+def dev_residues(torch, n, q, width, gen, dev):
+    """n residues uniform in [0, q) generated on the device (rejection on bitlen(q)-bit draws)."""
+    bits = q.bit_length()
+
+    def draw64(m):
+        a = torch.empty(m, dtype=torch.int64, device=dev).random_(generator=gen)
+        b = torch.empty(m, dtype=torch.int64, device=dev).random_(generator=gen)
+        return (a & 0xFFFFFFFF) | (b << 32)
+
+    if width == 1:
+        mask = (1 << bits) - 1
+        x = draw64(n) & mask
+        while True:
+            bad = x >= q
+            k = int(bad.sum())
+            if k == 0:
+                return x
+            x[bad] = draw64(k) & mask
+    qlo, qhi = q & (2**64 - 1), q >> 64
+    sign = -(2**63)
+    qlo_s = (qlo ^ (1 << 63)) - (1 << 64) if (qlo ^ (1 << 63)) >= (1 << 63) else (qlo ^ (1 << 63))
+    hmask = (1 << (bits - 64)) - 1
+    out = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    lo, hi = draw64(n), draw64(n) & hmask
+    while True:
+        lo_s = lo ^ sign
+        bad = (hi > qhi) | ((hi == qhi) & (lo_s >= qlo_s))
+        k = int(bad.sum())
+        if k == 0:
+            break
+        lo[bad] = draw64(k)
+        hi[bad] = draw64(k) & hmask
+    out[:, 0], out[:, 1] = lo, hi
+    return out
+
+
+def uneven_mix(M, torch, dev, seed=4):
+    """512 transforms (N uniform over 2^12..2^17, 60- or 124-bit prime q = 1 mod 2^18 of their own,
+    forward then inverse) interleaved with 512 BLAS jobs (vmul or axpy, length 2^k with k uniform
+    in 14..22, 60- or 124-bit).  Returns jobs for the batch form and work counts."""
+    from paper_2509_12494_gb300 import workload as W
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    ntt, blas = [], []
+    for i in range(512):
+        log2n = int(rng.integers(12, 18))
+        bits = int(rng.choice([60, 124]))
+        width = 2 if bits > 60 else 1
+        q = W.gen_prime(bits, 18, 10000 + i)
+        psi = W.gen_root(q, log2n, i)
+        plan = M.ntt_plan_create(log2n, q, psi, width, M.MQ_ORDER_BITREV)
+        d = dev_residues(torch, 1 << log2n, q, width, gen, dev)
+        ntt.append(dict(plan=plan, d=d, N=1 << log2n, log2n=log2n))
+    for i in range(512):
+        k = int(rng.integers(14, 23))
+        bits = int(rng.choice([60, 124]))
+        width = 2 if bits > 60 else 1
+        q = W.gen_prime(bits, 18, 20000 + i)
+        n = 1 << k
+        op = "vmul" if rng.integers(0, 2) == 0 else "axpy"
+        a = dev_residues(torch, n, q, width, gen, dev)
+        b = dev_residues(torch, n, q, width, gen, dev)
+        c = torch.empty_like(a) if op == "vmul" else b
+        s = int(rng.integers(1, 2**62)) % q
+        blas.append(dict(op=op, a=a, b=b, c=c, n=n, q=q, width=width, s=s))
+    jobs = []
+    for i in range(512):   # interleaved: forward i, its inverse, BLAS i
+        t = ntt[i]
+        jobs.append(M.ntt_job(M.MQ_JOB_NTT_FORWARD, t["plan"], t["d"], 1, t["N"]))
+        jobs.append(M.ntt_job(M.MQ_JOB_NTT_INVERSE, t["plan"], t["d"], 1, t["N"], after=len(jobs) - 1))
+        bj = blas[i]
+        kind = M.MQ_JOB_VMUL if bj["op"] == "vmul" else M.MQ_JOB_AXPY
+        jobs.append(M.blas_job(kind, bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], bj["s"]))
+    bfly = sum(2 * (t["N"] // 2) * t["log2n"] for t in ntt)
+    mm = sum(b["n"] for b in blas)
+    return dict(ntt=ntt, blas=blas, jobs=jobs, butterflies=bfly, blas_modmuls=mm)
+
+
+def bench_uneven(M, torch, dev, stream, flush, steps):
+    mix = uneven_mix(M, torch, dev)
+    sh = stream.cuda_stream
+    b = M.mq_batch_create(mix["jobs"], stream=sh)
+    info = M.mq_batch_info(b)
+
+    def step_batch():
+        M.mq_batch_launch(b, stream=sh)
+
+    def step_calls():
+        for t, bj in zip(mix["ntt"], mix["blas"]):
+            M.ntt_forward(t["plan"], t["d"], 1, t["N"], stream=sh)
+            M.ntt_inverse(t["plan"], t["d"], 1, t["N"], stream=sh)
+            if bj["op"] == "vmul":
+                M.mod_vmul(bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], stream=sh)
+            else:
+                M.mod_axpy(bj["c"], bj["s"], bj["a"], bj["n"], bj["q"], bj["width"], stream=sh)
+
+    def timeit(step, k):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(k):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                flush_l2(flush)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+        return statistics.median([x.elapsed_time(y) for x, y in ts])
+
+    ms_b = timeit(step_batch, max(3, steps))
+    status = M.mq_batch_status(b)
+    ms_c = timeit(step_calls, max(2, steps // 2))
+    total = mix["butterflies"] + mix["blas_modmuls"]
+    return {"workload": "uneven batch: 512 negacyclic NTTs (N uniform 2^12..2^17, own 60/124-bit prime each, "
+                        "forward then inverse, bit-reversed order) interleaved with 512 vmul/axpy jobs "
+                        "(length 2^14..2^22, 60/124-bit)",
+            "modmul_per_s": total / (ms_b * 1e-3), "butterflies_per_s": mix["butterflies"] / (ms_b * 1e-3),
+            "blas_modmul_per_s": mix["blas_modmuls"] / (ms_b * 1e-3), "ms_per_step": ms_b, "status": status,
+            "items": info["items"], "per_call": {"modmul_per_s": total / (ms_c * 1e-3), "ms_per_step": ms_c,
+                                                 "launches": 512 + sum(2 * (1 if t["N"] <= 4096 else 2) for t in mix["ntt"])},
+            "batched_over_per_call": ms_c / ms_b, "butterflies": mix["butterflies"],
+            "blas_modmuls": mix["blas_modmuls"]}
+
+
+# ----------------------------------------------------------------------------------- serving
+
+def run_serve(args):
+    """Open-loop Poisson arrivals of single requests drawn from the uneven mix (a forward or an
+    inverse transform, or a BLAS job), at a geometric sweep of rates, through the batching server
+    and through the plain per-call mode.  A request's buffers are not reused while it is in flight
+    (a busy buffer delays that arrival, which only happens near saturation)."""
+    import torch
+
+    from paper_2509_12494_gb300 import mqntt as M
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    M.load(build_if_missing=True)
+    mix = uneven_mix(M, torch, dev, seed=5)
+    pool = []
+    for t in mix["ntt"]:
+        pool.append(M.ntt_job(M.MQ_JOB_NTT_FORWARD, t["plan"], t["d"], 1, t["N"]))
+    for bj in mix["blas"]:
+        kind = M.MQ_JOB_VMUL if bj["op"] == "vmul" else M.MQ_JOB_AXPY
+        pool.append(M.blas_job(kind, bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], bj["s"]))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    pool = [pool[i] for i in rng.permutation(len(pool))]
+    out = {"metric": METRIC, "impl": "mq", "workload": "serve", "unit": "requests/s",
+           "config": {"workload": "serving: Poisson arrivals of single NTT (2^12..2^17, 60/124-bit) and "
+                                  "vmul/axpy (2^14..2^22) requests, twiddles and operands resident, "
+                                  "admission by free HBM", "seconds_per_rate": args.serve_seconds},
+           "points": []}
+
+    def run(mode, rate, n_req, seed):
+        srv = M.mq_server_create(M.mq_server_cfg(mode=mode))
+        offered = M.mq_server_poisson(srv, pool, rate, n_req, seed)
+        M.mq_server_drain(srv, 300)
+        st = M.mq_server_stats(srv)
+        M.mq_server_destroy(srv)
+        return offered, st
+
+    # saturated throughput of each mode: everything submitted at once
+    sat = {}
+    for mode_name, mode in (("batched", M.MQ_SERVE_BATCHED), ("plain", M.MQ_SERVE_PLAIN)):
+        _, st = run(mode, 0.0, 4 * len(pool), 1)
+        sat[mode_name] = st["jobs_per_s"]
+    out["saturated_jobs_per_s"] = sat
+    base = sat["batched"]
+    for mode_name, mode in (("batched", M.MQ_SERVE_BATCHED), ("plain", M.MQ_SERVE_PLAIN)):
+        for frac in (0.1, 0.2, 0.35, 0.5, 0.7, 0.85, 1.0, 1.25, 1.5):
+            rate = frac * base
+            n_req = int(max(200, min(rate * args.serve_seconds, 200000)))
+            offered, st = run(mode, rate, n_req, 7)
+            out["points"].append({"mode": mode_name, "rate_frac_of_batched_saturation": frac, "rate": rate,
+                                  "offered_per_s": offered, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                                  "jobs_per_s": st["jobs_per_s"], "modmul_per_s": st["modmul_per_s"],
+                                  "butterflies_per_s": st["butterflies_per_s"],
+                                  "mean_batch_jobs": st["mean_batch_jobs"], "failed": st["failed"]})
+    return out
 
 
 # ----------------------------------------------------------------------------------- oracle arms
@@ -434,6 +628,8 @@ def main():
             dist.init_process_group("nccl")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "serve":
+        out = run_serve(args) if rank == 0 else None
     else:
         out = run_gpu(args, rank, world)
         if out is not None and not args.no_cpu_baseline:

@@ -69,6 +69,16 @@ int mq_wait(mq_server *s, uint64_t ticket, double timeout_s, int *status);
 /* Block until every submitted ticket finished (MQ_ERR_TIMEOUT after `timeout_s`). */
 int mq_server_drain(mq_server *s, double timeout_s);
 
+/*
+ * Open-loop load generator: submit `n_requests` requests taken round-robin from `pool`, with
+ * exponential inter-arrival times of mean 1/rate_per_s (a Poisson process drawn from `seed`;
+ * rate_per_s <= 0 submits as fast as possible).  A pool entry is resubmitted only after its
+ * previous request finished (its buffers are reused).  Returns once all are submitted, with the
+ * achieved submission rate in *offered_per_s (may be NULL); use mq_server_drain to wait for them.
+ */
+int mq_server_poisson(mq_server *s, const mq_job *pool, size_t npool, double rate_per_s, uint64_t n_requests,
+                      uint64_t seed, double *offered_per_s);
+
 /* Statistics over the tickets completed since creation or the last reset. */
 int mq_server_stats(mq_server *s, mq_stats *out);
 int mq_server_reset_stats(mq_server *s);

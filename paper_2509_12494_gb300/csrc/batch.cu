@@ -521,6 +521,11 @@ int mq::batch_detail::refill_jobs(const mq_job *jobs, size_t njobs, const mq_bat
     return MQ_OK;
 }
 
+int mq::batch_detail::check_job(const mq_job &j, const mq_batch_opts &opts) {
+    JobDev d;
+    return fill_job(j, 0, opts, (void *)(uintptr_t)256, d);  // stand-in staging pointer, never dereferenced
+}
+
 int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
                                    unsigned long long grid_items, BatchTables &out) {
     out.jobs.assign(njobs, JobDev());

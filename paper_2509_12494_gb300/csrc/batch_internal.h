@@ -55,6 +55,9 @@ size_t job_scratch_bytes(const mq_job &j);
 int build_tables(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
                  unsigned long long grid_items, BatchTables &out);
 
+// Validate one job on its own (as job 0 of a batch): MQ_OK or an MQ_ERR_* code (message set).
+int check_job(const mq_job &j, const mq_batch_opts &opts);
+
 // Re-fill the descriptors of an already built batch with new pointers / scalars (same shapes).
 int refill_jobs(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
                 std::vector<JobDev> &jobs_io);

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -391,12 +392,8 @@ extern "C" int mq_submit(mq_server *srv, const mq_job *job, uint64_t *ticket) {
     Server *s = srv->impl;
     if (job->after != -1) return mq_fail(MQ_ERR_ARG, "served jobs are independent: `after` must be -1");
     if (is_ntt_kind(job->kind) && !job->plan) return mq_fail(MQ_ERR_ARG, "NTT job without a plan");
-    // full validation through the batch table builder (with a stand-in staging pointer)
     {
-        mq_job j = *job;
-        BatchTables t;
-        void *dummy = (void *)(uintptr_t)256;
-        int rc = build_tables(&j, 1, s->opts, &dummy, 1, t);
+        int rc = check_job(*job, s->opts);  // everything a batch would check about this job
         if (rc) return rc;
     }
     Ticket t;
@@ -415,6 +412,42 @@ extern "C" int mq_submit(mq_server *srv, const mq_job *job, uint64_t *ticket) {
         s->pending.push_back(*ticket);
     }
     s->cv.notify_all();
+    return MQ_OK;
+}
+
+// splitmix64: a small seeded generator for the arrival process
+static uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" int mq_server_poisson(mq_server *srv, const mq_job *pool, size_t npool, double rate_per_s,
+                                 uint64_t n_requests, uint64_t seed, double *offered_per_s) {
+    if (!srv || !pool || !npool) return mq_fail(MQ_ERR_ARG, "NULL or empty request pool");
+    std::vector<uint64_t> last(npool, 0);
+    uint64_t st = seed;
+    const uint64_t t0 = now_ns();
+    double t_next = 0.0;  // ns after t0
+    for (uint64_t i = 0; i < n_requests; ++i) {
+        if (rate_per_s > 0) {
+            // exponential inter-arrival time by inversion of a uniform draw in (0, 1]
+            const double u = ((double)(splitmix64(st) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+            t_next += -std::log(u) / rate_per_s * 1e9;
+            while ((double)(now_ns() - t0) < t_next) {
+            }
+        }
+        const size_t k = (size_t)(i % npool);
+        if (last[k]) {  // a request's buffers are not reused while it is in flight
+            int status = 0;
+            int rc = mq_wait(srv, last[k], 600.0, &status);
+            if (rc) return rc;
+        }
+        int rc = mq_submit(srv, &pool[k], &last[k]);
+        if (rc) return rc;
+    }
+    if (offered_per_s) *offered_per_s = (double)n_requests / ((double)(now_ns() - t0) * 1e-9);
     return MQ_OK;
 }
 

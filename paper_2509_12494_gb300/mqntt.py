@@ -77,6 +77,8 @@ def load(build_if_missing: bool = False):
         "mq_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "mq_wait": [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)],
         "mq_server_drain": [_vp, ctypes.c_double],
+        "mq_server_poisson": [_vp, _vp, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                              ctypes.POINTER(ctypes.c_double)],
         "mq_server_stats": [_vp, _vp],
         "mq_server_reset_stats": [_vp],
         "mq_server_destroy": [_vp],
@@ -359,6 +361,15 @@ def mq_wait(server: Server, ticket: int, timeout_s: float = 60.0) -> int:
 
 def mq_server_drain(server: Server, timeout_s: float = 120.0):
     _check(load().mq_server_drain(server.handle, timeout_s))
+
+
+def mq_server_poisson(server: Server, jobs, rate_per_s: float, n_requests: int, seed: int = 1) -> float:
+    """Open-loop Poisson submission from a native thread; returns the achieved offered rate."""
+    arr = _job_array(jobs)
+    off = ctypes.c_double()
+    _check(load().mq_server_poisson(server.handle, ctypes.cast(arr, _vp), len(jobs), rate_per_s, n_requests, seed,
+                                    ctypes.byref(off)))
+    return off.value
 
 
 def mq_server_stats(server: Server) -> dict:
