@@ -76,6 +76,35 @@ def workload_name(wl, args):
             f"{args.bits}-bit q = 1 mod 2^{wl['log2n'] + 1}, {args.order} order")
 
 
+KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "blas_ops.cuh", "batch_internal.h", "batch.cu"]
+
+
+def kernel_sources_sha256() -> str:
+    """Hash of the sources that define the persistent kernel (to tell whether a profile is current)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_12494_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(summary: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
+                k, v = line.strip().split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_sources_sha256") == kernel_sources_sha256():
+            return float(fields["traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -131,6 +160,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(busy or sm) if (busy or sm) else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows),
                 "samples_busy": len(busy)}
+
+
+# ----------------------------------------------------------------------------------- replicas
+
+def aggregate(ms_local: float, units_local: float, world: int, device=None):
+    """Whole-job throughput of `world` independent replicas (weak scaling): the slowest rank's
+    time and all ranks' units; returns (ms, units per second).  No data crosses ranks."""
+    if world == 1:
+        return ms_local, units_local / (ms_local * 1e-3)
+    import torch
+    import torch.distributed as dist
+    ms = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    units = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    ms_max = float(ms.item())
+    return ms_max, float(units.item()) / (ms_max * 1e-3)
 
 
 # ----------------------------------------------------------------------------------- GPU arm
@@ -225,13 +271,8 @@ def run_gpu(args, rank, world):
     with ClockSampler(dev.index) as clk:
         t_batched = timed(step_batched, args.steps, args.warmup)
         clocks = clk.summary()
-    ms = sum(t_batched) / len(t_batched)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     bfly = 2 * wl["butterflies_per_dir"]
-    value = bfly * world / (ms * 1e-3)
+    ms, value = aggregate(sum(t_batched) / len(t_batched), bfly, world, dev)
 
     # correctness of what was timed: the round trip leaves the input unchanged
     batch_status = M.mq_batch_status(pbatch)
@@ -293,7 +334,8 @@ def run_gpu(args, rank, world):
     alu_frac, hbm_frac = alu_achieved / alu_peak, hbm_achieved / hbm_peak
     if alu_frac >= hbm_frac:
         out["roofline"] = {"bound": "alu", "achieved": alu_achieved / 1e12, "peak": alu_peak / 1e12,
-                           "unit": "T mad32/s", "frac": alu_frac, "traffic": None,
+                           "unit": "T mad32/s", "frac": alu_frac,
+                           "traffic": profiled_traffic(f"persistent_kernel_uniform_{batch}x{N}_{args.bits}bit.md"),
                            "kernel": "persistent_kernel (one launch = one step)",
                            "peak_source": "measured by mq_probe_imad_rate (carry-chained mad.lo.cc/madc.hi.cc)",
                            "algorithmic": f"{mads_per_mul} 32-bit multiply instructions per Shoup product",
@@ -301,7 +343,9 @@ def run_gpu(args, rank, world):
                            "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src, "ms_launch": ms_launch}
     else:
         out["roofline"] = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                           "frac": hbm_frac, "traffic": None, "kernel": "persistent_kernel (one launch = one step)",
+                           "frac": hbm_frac,
+                           "traffic": profiled_traffic(f"persistent_kernel_uniform_{batch}x{N}_{args.bits}bit.md"),
+                           "kernel": "persistent_kernel (one launch = one step)",
                            "peak_source": hbm_src, "alu_frac": alu_frac, "ms_launch": ms_launch,
                            "alu_achieved_tmads": alu_achieved / 1e12, "alu_peak_tmads": alu_peak / 1e12}
     out["roofline"]["call_form_alu_frac"] = (mad_f + mad_i) / ((ms_f + ms_i) * 1e-3) / alu_peak
