@@ -200,7 +200,7 @@ __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned lon
 template <int W, int L, int RR, bool INV, int BAR = 0>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
                                             int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
-                                            typename Traits<W>::E q2) {
+                                            typename Traits<W>::E q4) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
     typedef Shape<W, L> S;
@@ -233,20 +233,20 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                 E w, wp;
                 if (!INV) {
                     Tr::load_tw(tw, idx, w, wp);
-                    E uu = csub(u, q2);                              // [0, 2q)
-                    E tv = mul_mod_shoup_lazy(v, w, wp, q);          // [0, 2q)
-                    u = add_nored(uu, tv);                           // [0, 4q)
-                    v = add_sub(uu, q2, tv);                         // (0, 4q)
+                    E uu = csub(u, q4);                              // [0, 4q)
+                    E tv = mul_mod_shoup_lazy(v, w, wp, q);          // [0, 3q)
+                    u = add_nored(uu, tv);                           // [0, 7q)
+                    v = add_sub(uu, q4, tv);                         // (q, 8q)
                 } else if (s == 0 && a.scale) {
-                    E dif = add_sub(u, q2, v);                       // (0, 4q)
-                    E sum = add_nored(u, v);                         // [0, 4q)
+                    E dif = add_sub(u, q4, v);                       // (0, 8q)
+                    E sum = add_nored(u, v);                         // [0, 8q)
                     u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q);
                     v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q);
                 } else {
                     Tr::load_tw(tw, idx, w, wp);
-                    E dif = add_sub(u, q2, v);                       // (0, 4q)
-                    u = csub(add_nored(u, v), q2);                   // [0, 2q)
-                    v = mul_mod_shoup_lazy(dif, w, wp, q);           // [0, 2q)
+                    E dif = add_sub(u, q4, v);                       // (0, 8q)
+                    u = csub(add_nored(u, v), q4);                   // [0, 4q)
+                    v = mul_mod_shoup_lazy(dif, w, wp, q);           // [0, 3q)
                 }
             }
         }
@@ -264,11 +264,12 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
 // Called by NT = Shape::NT threads with thread index tid after a barrier that follows the staging;
 // ends with a barrier, after which `sm` may be refilled.
 //
-// Butterflies are lazy (Harvey): between stages the values stay below 4q (forward) or 2q
-// (inverse) and Shoup products skip their final correction; the pass flagged `final`
-// canonicalises what it stores.  q < 2^124 (2^60) keeps 4q below the word size.
-//   forward (CT):  u <- u mod 2q;  t = w v mod q + {0, q};  (u, v) <- (u + t, u + 2q - t)
-//   inverse (GS):  (u, v) <- ((u + v) mod 2q, (u + 2q - v) w mod q + {0, q})
+// Butterflies are lazy (after Harvey): between stages the values stay below 8q (forward) or 4q
+// (inverse), and twiddle products are left in [0, 3q) (128-bit: Shoup with a truncated quotient;
+// 64-bit: Shoup without its final correction, [0, 2q)); the pass flagged `final` canonicalises
+// what it stores.  q < 2^124 (2^60) keeps 8q below the word size.
+//   forward (CT):  u <- u mod 4q;  t = w v mod q + {0, q, 2q};  (u, v) <- (u + t, u + 4q - t)
+//   inverse (GS):  (u, v) <- ((u + v) mod 4q, (u + 4q - v) w mod q + {0, q, 2q})
 // Global loads and stores go through L2 only (.cg), so a pass may read what another SM wrote
 // earlier in the same kernel once the writer's completion is observed.
 template <int W, int L, bool INV, int BAR = 0>
@@ -280,6 +281,7 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
 
     const E q = Tr::make(a.q);
     const E q2 = add_nored(q, q);
+    const E q4 = add_nored(q2, q2);
     const int L1 = a.L1, logN = a.logN;
     const TileAddr ta(a);
     const int lgTP = ta.lgTP;
@@ -301,12 +303,12 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
     constexpr int FULL = L / S::r, PART = L - FULL * S::r;
     if (!INV) {
 #pragma unroll 1
-        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q2);
-        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q2);
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
+        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
     } else {
-        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q2);
+        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
 #pragma unroll 1
-        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q2);
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
     }
 
     // ---- shared -> global (canonical residues from the last pass)
@@ -319,7 +321,8 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
         if (poly < a.batch) {
             E v = sm[gg * S::TS + swz<W>(l)];
             if (a.final) {
-                if (!INV) v = csub(v, q2);  // forward values are below 4q
+                if (!INV) v = csub(v, q4);  // forward values are below 8q, inverse ones below 4q
+                v = csub(v, q2);
                 v = csub(v, q);
             }
             st_cg(out + poly * a.out_stride + tile_pos(a.out_layout, ti, l, L, L1, logN, a.perm), v);

@@ -52,8 +52,9 @@ __device__ __forceinline__ uint64_t mul_mod_shoup(uint64_t a, uint64_t w, uint64
     return (r >= q) ? r - q : r;
 }
 
+// a * w mod q up to one multiple of q: in [0, 2q) (the final Shoup correction skipped).
 __device__ __forceinline__ uint64_t mul_mod_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t q) {
-    return a * w - __umul64hi(a, wp) * q;  // in [0, 2q)
+    return a * w - __umul64hi(a, wp) * q;
 }
 __device__ __forceinline__ uint64_t csub(uint64_t a, uint64_t m) { return a >= m ? a - m : a; }
 __device__ __forceinline__ uint64_t add_nored(uint64_t a, uint64_t b) { return a + b; }
@@ -230,15 +231,65 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
     return reduce_once(r, q);
 }
 
-// a * w mod q up to one multiple of q: the result is in [0, 2q).  Shoup's quotient estimate is
-// the true quotient or one less, so skipping the final correction leaves at most one extra q.
-// a may be any value below 2^128 (lazy butterflies feed it values below 4q).
+// floor((a * b - D) / 2^128) where D = a0 b0 + 2^32 (a0 b1 + a1 b0) < 2^98: the high half of the
+// product without the three limb products that only reach columns 0..2.  Since D < 2^128 the
+// result is the true high half or one less.  26 multiply instructions instead of 32 (13 of them
+// high halves instead of 16), in the even/odd chains of mul_wide.
+__device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
+    uint32_t E2, E3, E4, E5, E6, O2, O3, O4, O5, O6, O7;
+    // row 0 (b0): only a2 b0 -> columns 2, 3 and a3 b0 -> columns 3, 4
+    asm("mul.lo.u32 %0, %4, %6;\n\t"
+        "mul.hi.u32 %1, %4, %6;\n\t"
+        "mul.lo.u32 %2, %5, %6;\n\t"
+        "mul.hi.u32 %3, %5, %6;"
+        : "=r"(E2), "=r"(E3), "=r"(O3), "=r"(O4)
+        : "r"(a.z), "r"(a.w), "r"(b.x));
+    // row 1 (b1): a2 b1 -> 3, 4 (even chain); a1 b1 -> 2, 3 and a3 b1 -> 4, 5 (odd chain)
+    asm("mad.lo.cc.u32  %0, %6, %8, %0;\n\t"
+        "madc.hi.u32    %1, %6, %8, 0;\n\t"
+        "mul.lo.u32     %2, %7, %8;\n\t"
+        "mad.hi.cc.u32  %3, %7, %8, %3;\n\t"
+        "madc.lo.cc.u32 %4, %9, %8, %4;\n\t"
+        "madc.hi.u32    %5, %9, %8, 0;"
+        : "+r"(E3), "=r"(E4), "=r"(O2), "+r"(O3), "+r"(O4), "=r"(O5)
+        : "r"(a.z), "r"(a.y), "r"(b.y), "r"(a.w));
+#define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
+    asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
+        "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \
+        "madc.lo.cc.u32 %2, %10, %12, %2;\n\t"                                                \
+        "madc.hi.u32    %3, %10, %12, 0;\n\t"                                                 \
+        "mad.lo.cc.u32  %4, %9, %12, %4;\n\t"                                                 \
+        "madc.hi.cc.u32 %5, %9, %12, %5;\n\t"                                                 \
+        "madc.lo.cc.u32 %6, %11, %12, %6;\n\t"                                                \
+        "madc.hi.u32    %7, %11, %12, 0;"                                                       \
+        : "+r"(e0), "+r"(e1), "+r"(e2), "=r"(e3), "+r"(o1), "+r"(o2), "+r"(o3), "=r"(o4)       \
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(bi));
+    MQ_ROW(E2, E3, E4, E5, O3, O4, O5, O6, b.z)
+    MQ_ROW(E3, E4, E5, E6, O4, O5, O6, O7, b.w)
+#undef MQ_ROW
+    uint4 r;
+    uint32_t c2, c3;
+    asm("add.cc.u32  %0, %6, %12;\n\t"
+        "addc.cc.u32 %1, %7, %13;\n\t"
+        "addc.cc.u32 %2, %8, %14;\n\t"
+        "addc.cc.u32 %3, %9, %15;\n\t"
+        "addc.cc.u32 %4, %10, %16;\n\t"
+        "addc.u32    %5, %11, %17;"
+        : "=r"(c2), "=r"(c3), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "r"(E2), "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(0u), "r"(O2), "r"(O3), "r"(O4), "r"(O5), "r"(O6),
+          "r"(O7));
+    (void)c2;
+    (void)c3;
+    return r;
+}
+
+// a * w mod q up to two multiples of q: the result is in [0, 3q).  Shoup's quotient estimate is the
+// true quotient or one less, and the truncated high half takes at most one more away.  a may be any
+// value below 2^128 (lazy butterflies feed it values below 8q).
 __device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q) {
-    uint32_t h[8];
-    mul_wide(a, wp, h);
-    uint4 qhat = make_uint4(h[4], h[5], h[6], h[7]);
+    uint4 qhat = mul_hi_trunc(a, wp);
     uint32_t m;
-    return sub128(mul_lo(a, w), mul_lo(qhat, q), m);
+    return sub128(mul_lo(a, w), mul_lo(qhat, q), m);  // exact: a w - qhat q < 3q < 2^126
 }
 
 // a >= m ? a - m : a
