@@ -17,6 +17,9 @@ extern "C" {
 #define MQ_PROBE_MAD_LO 0 /* independent mad.lo.u32 chains */
 #define MQ_PROBE_MAD_HI 1 /* independent mad.hi.u32 chains */
 #define MQ_PROBE_MAD_CC 2 /* carry-chained mad.lo.cc / madc.hi.cc pairs */
+#define MQ_PROBE_MAD_WIDE 3 /* independent mad.wide.u32 chains (32 x 32 + 64 -> 64) */
+#define MQ_PROBE_MAD_HI_CC 4 /* independent mad.hi.cc.u32 chains (carry flag written, unused) */
+#define MQ_PROBE_MAD_LO_HI_END 5 /* pairs mad.lo.cc + madc.hi (no carry-out), a row's last limb */
 
 /*
  * Run `iters` loop iterations of the chosen multiply-add pattern on every SM (one full wave of

@@ -38,6 +38,40 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_kernel(uint32_t *out, int
                 for (int i = 0; i < CHAINS; ++i) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(b), "r"(c[i]));
             }
         }
+    } else if (kind == MQ_PROBE_MAD_WIDE) {  // 32 x 32 -> 64 multiply-adds, 64-bit accumulators
+        unsigned long long w[CHAINS];
+#pragma unroll
+        for (int i = 0; i < CHAINS; ++i) w[i] = ((unsigned long long)c[i] << 32) | a[i];
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) {
+#pragma unroll
+                for (int i = 0; i < CHAINS; ++i) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[i]) : "r"(b), "r"(c[i]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CHAINS; ++i) a[i] = (uint32_t)(w[i] ^ (w[i] >> 32));
+    } else if (kind == MQ_PROBE_MAD_HI_CC) {  // high halves that write the carry flag
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < UNROLL; ++k) {
+#pragma unroll
+                for (int i = 0; i < CHAINS; ++i) asm volatile("mad.hi.cc.u32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(b), "r"(c[i]));
+            }
+        }
+    } else if (kind == MQ_PROBE_MAD_LO_HI_END) {  // mad.lo.cc then madc.hi without carry-out
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < UNROLL / 2; ++k) {
+#pragma unroll
+                for (int i = 0; i < CHAINS; i += 2)
+                    asm volatile(
+                        "mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
+                        "madc.hi.u32    %1, %2, %3, %1;"
+                        : "+r"(a[i]), "+r"(a[i + 1])
+                        : "r"(c[i]), "r"(b));
+            }
+        }
     } else {  // carry-chained pairs, the shape of the schoolbook product rows
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
@@ -63,7 +97,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_kernel(uint32_t *out, int
 }  // namespace
 
 extern "C" int mq_probe_imad_rate(int kind, int iters, double *inst_per_s, double *ms, void *stream) {
-    if (kind < MQ_PROBE_MAD_LO || kind > MQ_PROBE_MAD_CC) return mq_fail(-1, "unknown probe kind %d", kind);
+    if (kind < MQ_PROBE_MAD_LO || kind > MQ_PROBE_MAD_LO_HI_END) return mq_fail(-1, "unknown probe kind %d", kind);
     if (iters <= 0 || !inst_per_s) return mq_fail(-1, "iters must be positive and inst_per_s non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0, per_sm = 0;

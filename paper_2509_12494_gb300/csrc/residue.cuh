@@ -134,6 +134,14 @@ __device__ __forceinline__ uint4 sub_mod(uint4 a, uint4 b, uint4 q) {
     return add128(d, and128(q, m));  // add q back only when a < b
 }
 
+// 32 x 32 -> 64-bit product as (lo, hi): one full-rate wide multiply (a separate high-half multiply
+// issues at half the rate of a low-half one on this GPU).
+__device__ __forceinline__ void mul_wide32(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+    const unsigned long long p = (unsigned long long)a * b;
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
 // Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  The 16 limb products
 // are accumulated in two carry chains: E takes the products of the even limbs a0, a2 and O those
 // of the odd limbs a1, a3, so that within one row (one limb b_i) the lo and hi halves of a chain
@@ -142,16 +150,10 @@ __device__ __forceinline__ uint4 sub_mod(uint4 a, uint4 b, uint4 q) {
 // needed.  A final 7-limb addition merges the two chains: 32 multiply instructions and 7 adds.
 __device__ __forceinline__ void mul_wide(const uint4 a, const uint4 b, uint32_t c[8]) {
     uint32_t E0, E1, E2, E3, E4, E5, E6, O1, O2, O3, O4, O5, O6, O7;
-    asm("mul.lo.u32 %0, %8, %12;\n\t"
-        "mul.hi.u32 %1, %8, %12;\n\t"
-        "mul.lo.u32 %2, %10, %12;\n\t"
-        "mul.hi.u32 %3, %10, %12;\n\t"
-        "mul.lo.u32 %4, %9, %12;\n\t"
-        "mul.hi.u32 %5, %9, %12;\n\t"
-        "mul.lo.u32 %6, %11, %12;\n\t"
-        "mul.hi.u32 %7, %11, %12;"
-        : "=r"(E0), "=r"(E1), "=r"(E2), "=r"(E3), "=r"(O1), "=r"(O2), "=r"(O3), "=r"(O4)
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x));
+    mul_wide32(a.x, b.x, E0, E1);  // row 0: four disjoint 64-bit products, no additions
+    mul_wide32(a.z, b.x, E2, E3);
+    mul_wide32(a.y, b.x, O1, O2);
+    mul_wide32(a.w, b.x, O3, O4);
 #define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
     asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
         "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \
@@ -183,13 +185,11 @@ __device__ __forceinline__ void mul_wide(const uint4 a, const uint4 b, uint32_t 
 // Low 128 bits of a * b: only the products that reach columns 0..3.
 __device__ __forceinline__ uint4 mul_lo(const uint4 a, const uint4 b) {
     uint32_t e0, e1, e2, e3, o1, o2, o3;
-    // even limbs (a0, a2)
-    asm("mul.lo.u32 %0, %4, %6;\n\t"
-        "mul.hi.u32 %1, %4, %6;\n\t"
-        "mul.lo.u32 %2, %5, %6;\n\t"
-        "mul.hi.u32 %3, %5, %6;"
-        : "=r"(e0), "=r"(e1), "=r"(e2), "=r"(e3)
-        : "r"(a.x), "r"(a.z), "r"(b.x));
+    // row 0: a0 b0 -> 0, 1; a2 b0 -> 2, 3; a1 b0 -> 1, 2; lo(a3 b0) -> 3
+    mul_wide32(a.x, b.x, e0, e1);
+    mul_wide32(a.z, b.x, e2, e3);
+    mul_wide32(a.y, b.x, o1, o2);
+    o3 = a.w * b.x;
     asm("mad.lo.cc.u32  %0, %3, %5, %0;\n\t"
         "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
         "madc.lo.u32    %2, %4, %5, %2;"
@@ -201,11 +201,6 @@ __device__ __forceinline__ uint4 mul_lo(const uint4 a, const uint4 b) {
         : "r"(a.x), "r"(b.z));
     asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(e3) : "r"(a.x), "r"(b.w));
     // odd limbs (a1, a3), one column up
-    asm("mul.lo.u32 %0, %3, %5;\n\t"
-        "mul.hi.u32 %1, %3, %5;\n\t"
-        "mul.lo.u32 %2, %4, %5;"
-        : "=r"(o1), "=r"(o2), "=r"(o3)
-        : "r"(a.y), "r"(a.w), "r"(b.x));
     asm("mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
         "madc.hi.u32    %1, %2, %3, %1;"
         : "+r"(o2), "+r"(o3)
@@ -236,23 +231,19 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
 // result is the true high half or one less.  26 multiply instructions instead of 32 (13 of them
 // high halves instead of 16), in the even/odd chains of mul_wide.
 __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
-    uint32_t E2, E3, E4, E5, E6, O2, O3, O4, O5, O6, O7;
+    uint32_t E2, E3, E4, E5, E6, O2, O3, O4, O5, O6, O7, h11;
     // row 0 (b0): only a2 b0 -> columns 2, 3 and a3 b0 -> columns 3, 4
-    asm("mul.lo.u32 %0, %4, %6;\n\t"
-        "mul.hi.u32 %1, %4, %6;\n\t"
-        "mul.lo.u32 %2, %5, %6;\n\t"
-        "mul.hi.u32 %3, %5, %6;"
-        : "=r"(E2), "=r"(E3), "=r"(O3), "=r"(O4)
-        : "r"(a.z), "r"(a.w), "r"(b.x));
+    mul_wide32(a.z, b.x, E2, E3);
+    mul_wide32(a.w, b.x, O3, O4);
     // row 1 (b1): a2 b1 -> 3, 4 (even chain); a1 b1 -> 2, 3 and a3 b1 -> 4, 5 (odd chain)
-    asm("mad.lo.cc.u32  %0, %6, %8, %0;\n\t"
-        "madc.hi.u32    %1, %6, %8, 0;\n\t"
-        "mul.lo.u32     %2, %7, %8;\n\t"
-        "mad.hi.cc.u32  %3, %7, %8, %3;\n\t"
-        "madc.lo.cc.u32 %4, %9, %8, %4;\n\t"
-        "madc.hi.u32    %5, %9, %8, 0;"
-        : "+r"(E3), "=r"(E4), "=r"(O2), "+r"(O3), "+r"(O4), "=r"(O5)
-        : "r"(a.z), "r"(a.y), "r"(b.y), "r"(a.w));
+    mul_wide32(a.y, b.y, O2, h11);
+    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
+        "madc.hi.u32    %1, %5, %7, 0;\n\t"
+        "add.cc.u32     %2, %2, %6;\n\t"
+        "madc.lo.cc.u32 %3, %8, %7, %3;\n\t"
+        "madc.hi.u32    %4, %8, %7, 0;"
+        : "+r"(E3), "=r"(E4), "+r"(O3), "+r"(O4), "=r"(O5)
+        : "r"(a.z), "r"(h11), "r"(b.y), "r"(a.w));
 #define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
     asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
         "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \

@@ -192,7 +192,7 @@ def mod_axpy(y, a: int, x, n: int, q: int, width: int, stream=None):
     _check(load().mod_axpy(ptr(y), words(a), ptr(x), n, words(q), width, stream_handle(stream)))
 
 
-MQ_PROBE_MAD_LO, MQ_PROBE_MAD_HI, MQ_PROBE_MAD_CC = 0, 1, 2
+MQ_PROBE_MAD_LO, MQ_PROBE_MAD_HI, MQ_PROBE_MAD_CC, MQ_PROBE_MAD_WIDE = 0, 1, 2, 3
 
 
 def mq_probe_imad_rate(kind: int, iters: int, stream=None):
