@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=1.5)
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
+    p.add_argument("--form", choices=["default", "split", "prefetch"], default="default",
+                   help="persistent kernel form (default: the library's choice for the batch)")
     return p.parse_args()
 
 
@@ -76,7 +78,8 @@ def workload_name(wl, args):
             f"{args.bits}-bit q = 1 mod 2^{wl['log2n'] + 1}, {args.order} order")
 
 
-KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "blas_ops.cuh", "batch_internal.h", "batch.cu"]
+KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "blas_ops.cuh", "batch_internal.h", "batch_kernel.cuh",
+                  "batch.cu"]
 
 
 def kernel_sources_sha256() -> str:
@@ -214,7 +217,9 @@ def run_gpu(args, rank, world):
     # the persistent batch: job i = forward of polynomial i, job batch + i = its inverse
     jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
     jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
-    opts = M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm) if (args.lag or args.ctas_per_sm) else None
+    form_flag = {"default": 0, "split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[args.form]
+    opts = (M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm, flags=form_flag)
+            if (args.lag or args.ctas_per_sm or form_flag) else None)
     pbatch = M.mq_batch_create(jobs, opts, stream=sh)
     pinfo = M.mq_batch_info(pbatch)
 

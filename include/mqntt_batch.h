@@ -47,7 +47,8 @@ typedef struct mq_job {
 
 /* batch creation options; zero-initialised fields take the defaults */
 typedef struct mq_batch_opts {
-    unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit, at most 2) */
+    unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit -- 2, or 3 for batches of 64-bit
+                              transforms only; larger values are clamped to that) */
     unsigned lag;          /* pipeline lag between dependent stages, in waves of the persistent grid (0: 2) */
     unsigned blas_chunk;   /* residues per BLAS work item (0: 16384); a multiple of 2048 */
     double wait_timeout_s; /* limit of every device-side wait (0: 2 s) */
@@ -58,6 +59,11 @@ typedef struct mq_batch_opts {
 #define MQ_BATCH_TEST_DROP_ITEM 2u /* fault injection for tests: leave out the first first-pass item of the
                                       first two-pass NTT job, so that its dependants' waits run out and
                                       mq_batch_status reports MQ_ERR_TIMEOUT */
+/* Kernel form (neither flag: the library's default for the batch's contents).  Both compute the same
+   results; they differ in how a CTA overlaps the loads of its next item with the current one. */
+#define MQ_BATCH_FORM_SPLIT 4u    /* warp-specialised: two producer warps stage items for eight compute warps */
+#define MQ_BATCH_FORM_PREFETCH 8u /* every warp computes; a CTA starts its next item's copies before the
+                                     current transform when that item's dependencies are already met */
 
 typedef struct mq_batch mq_batch;
 

@@ -33,6 +33,7 @@
 
 #include "../../include/mqntt_batch.h"
 #include "batch_internal.h"
+#include "batch_kernel.cuh"
 #include "blas_ops.cuh"
 #include "common.cuh"
 #include "hostmath.h"
@@ -46,272 +47,6 @@ int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv);
 namespace mq {
 namespace batch_detail {
 
-using ntt_detail::Shape;
-using ntt_detail::Traits;
-
-constexpr int BT = 256;               // threads per persistent CTA
-constexpr int LMIN = 6, LMAX = 11;    // tile sizes the persistent kernel carries
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_status(const unsigned *p) {
-    return (int)*(const volatile unsigned *)p;
-}
-
-// Bounded wait until *ctr >= target.  Returns false on timeout or when the batch already failed.
-__device__ bool wait_geq(const unsigned *ctr, unsigned target, const unsigned *status, unsigned long long limit_ns) {
-    if (ld_acquire(ctr) >= target) return true;
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        __nanosleep(200);
-        if (ld_acquire(ctr) >= target) return true;
-        if (ld_status(status) != 0) return false;
-        if (globaltimer() - t0 > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ uint4 u4(const uint64_t v[2]) {
-    return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
-}
-
-// residues [begin, end) of a BLAS job; 16-byte aligned operands (checked on the host)
-template <int W, int OP>
-__device__ __forceinline__ void blas_chunk(const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
-    if (W == 2) {
-        const Mod128 m{u4(b.q), u4(b.mu), b.L};
-        const uint4 s = u4(b.s), sp = u4(b.sp);
-        const uint4 *A = reinterpret_cast<const uint4 *>(b.a), *B = reinterpret_cast<const uint4 *>(b.b);
-        uint4 *C = reinterpret_cast<uint4 *>(b.c);
-        // one residue per thread and step: the wave of resident CTAs keeps enough loads in flight,
-        // and an unrolled Barrett would spill inside this many-branched kernel
-        for (unsigned long long i = begin + tid; i < end; i += BT) {
-            const uint4 va = __ldcg(A + i), vb = __ldcg(B + i);
-            __stcg(C + i, op128<OP>(va, vb, m, s, sp));
-        }
-    } else {
-        const Mod64 m{b.q[0], b.mu[0], b.L};
-        const uint64_t s = b.s[0], sp = b.sp[0];
-        // begin is a multiple of the (even) chunk: pairs first, then a possible odd last residue
-        const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(b.a), *B = reinterpret_cast<const ulonglong2 *>(b.b);
-        ulonglong2 *C = reinterpret_cast<ulonglong2 *>(b.c);
-        const unsigned long long vb0 = begin / 2, ve = end / 2;
-        for (unsigned long long i = vb0 + tid; i < ve; i += BT) {
-            ulonglong2 x = __ldcg(A + i), y = __ldcg(B + i), r;
-            r.x = op64<OP>(x.x, y.x, m, s, sp);
-            r.y = op64<OP>(x.y, y.y, m, s, sp);
-            __stcg(C + i, r);
-        }
-        if ((end & 1) && tid == 0) {
-            const unsigned long long *a1 = reinterpret_cast<const unsigned long long *>(b.a);
-            const unsigned long long *b1 = reinterpret_cast<const unsigned long long *>(b.b);
-            unsigned long long *c1 = reinterpret_cast<unsigned long long *>(b.c);
-            c1[end - 1] = op64<OP>(__ldcg(a1 + end - 1), __ldcg(b1 + end - 1), m, s, sp);
-        }
-    }
-}
-
-template <int W>
-__device__ __forceinline__ void run_blas(int op, const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
-    switch (op) {
-    case OP_VADD: blas_chunk<W, OP_VADD>(b, begin, end, tid); break;
-    case OP_VSUB: blas_chunk<W, OP_VSUB>(b, begin, end, tid); break;
-    case OP_VMUL: blas_chunk<W, OP_VMUL>(b, begin, end, tid); break;
-    default: blas_chunk<W, OP_AXPY>(b, begin, end, tid); break;
-    }
-}
-
-constexpr int PT = 64;              // producer threads (two warps)
-constexpr int CT = BT + PT;         // threads per persistent CTA
-constexpr int BAR_COMPUTE = 1;      // named barrier of the BT compute threads
-constexpr int BAR_FULL = 2;         // + buffer: producer -> compute, "buffer b holds item k"
-constexpr int BAR_EMPTY = 4;        // + buffer: compute -> producer, "buffer b is free again"
-constexpr int BAR_PRODUCER = 6;     // named barrier of the PT producer threads
-
-// named barriers with immediate ids (a register id would make ptxas reserve all sixteen)
-__device__ __forceinline__ void bar_arrive(int id) {
-    if (id == BAR_FULL) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
-    else if (id == BAR_FULL + 1) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
-    else if (id == BAR_EMPTY) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
-    else asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
-}
-__device__ __forceinline__ void bar_sync(int id) {
-    if (id == BAR_FULL) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
-    else if (id == BAR_FULL + 1) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
-    else if (id == BAR_EMPTY) asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
-    else asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
-}
-
-// Stage an item's tiles with the producer warps: cp.async through L2 for 128-bit residues, batched
-// L2 loads for 64-bit residues (an 8-byte cp.async would allocate in the non-coherent L1).
-template <int W>
-__device__ __forceinline__ void stage_tiles(int L, const PassArgs &a, unsigned long long first, void *sm, int lane) {
-    typedef typename Traits<W>::E E;
-    E *s = reinterpret_cast<E *>(sm);
-#define MQ_STAGE(LL)                                                                      \
-    if (W == 2) ntt_detail::load_tiles_async<W, LL, PT>(a, first, s, lane);               \
-    else ntt_detail::load_tiles_sync<W, LL, PT>(a, first, s, lane);                        \
-    break;
-    switch (L) {
-    case 6: MQ_STAGE(6)
-    case 7: MQ_STAGE(7)
-    case 8: MQ_STAGE(8)
-    case 9: MQ_STAGE(9)
-    case 10: MQ_STAGE(10)
-    default: MQ_STAGE(11)
-    }
-#undef MQ_STAGE
-}
-
-template <int W, bool INV>
-__device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned long long first, void *sm, int tid) {
-    typedef typename Traits<W>::E E;
-    E *s = reinterpret_cast<E *>(sm);
-    switch (L) {
-    case 6: ntt_detail::tile_compute_store<W, 6, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    case 7: ntt_detail::tile_compute_store<W, 7, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    case 8: ntt_detail::tile_compute_store<W, 8, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    case 9: ntt_detail::tile_compute_store<W, 9, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    case 10: ntt_detail::tile_compute_store<W, 10, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    default: ntt_detail::tile_compute_store<W, 11, INV, BAR_COMPUTE>(a, first, s, tid); break;
-    }
-}
-
-// ctrs: [0] next item, [1] status, [2, 2 + njobs) per-job finished items, then per-polynomial
-// finished first-pass items of two-pass transforms.
-//
-// Warp-specialised: warps 8-9 are the producer.  For item k it waits until buffer k % 2 is free,
-// takes the next item index, waits (bounded) for the item's dependencies, copies its arguments
-// and stages its tiles into the buffer, and hands it over.  Warps 0-7 compute and store the item,
-// publish its completion on the counters, and free the buffer.  The producer therefore runs one
-// item ahead, and its waits and loads overlap the transform of the previous item.
-__global__ void __launch_bounds__(CT, 2)
-    persistent_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
-                      unsigned *ctrs, unsigned njobs, unsigned long long limit_ns, size_t buf_bytes) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ PassArgs s_pa[2];
-    __shared__ BlasArgs s_ba[2];
-    __shared__ unsigned s_it[2];
-    __shared__ unsigned s_pit;
-    __shared__ int s_pok;
-    const int tid = threadIdx.x;
-    unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
-
-    if (tid >= BT) {  // ----------------------------------------------- producer warps
-        const int lane = tid - BT;  // 0 .. PT-1
-        for (unsigned k = 0;; ++k) {
-            const int b = k & 1;
-            if (k >= 2) bar_sync(BAR_EMPTY + b);
-            if (lane == 0) {
-                unsigned it0 = atomicAdd(ctrs, 1u);
-                if (ld_status(status) != 0) it0 = n_items;  // the batch failed: drain
-                int w = it0 < n_items;
-                if (w) {
-                    const ItemDev i0 = items[it0];
-                    const JobDev *J0 = jobs + i0.job;
-                    if (J0->kind == JK_NTT && J0->twopass && i0.pass == 1)
-                        w = wait_geq(poly_ctr + J0->poly_base + i0.poly, J0->groups0, status, limit_ns);
-                    else if (i0.pass == 0 && J0->after >= 0)
-                        w = wait_geq(job_ctr + J0->after, jobs[J0->after].n_items, status, limit_ns);
-                    if (!w) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
-                }
-                s_pit = it0;
-                s_pok = w;
-            }
-            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");
-            const unsigned it = s_pit;
-            const bool ok = s_pok != 0;
-            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");  // s_pit reusable
-            ItemDev item;
-            const JobDev *J = jobs;
-            if (ok) {
-                item = items[it];
-                J = jobs + item.job;
-            }
-            if (!ok) {  // end of the work (or a failed wait): tell the compute warps and stop
-                if (lane == 0) s_it[b] = n_items;
-                __threadfence_block();
-                bar_arrive(BAR_FULL + b);
-                break;
-            }
-            if (J->kind == JK_NTT) {
-                const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
-                unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
-                for (int w = lane; w < (int)(sizeof(PassArgs) / 4); w += PT) dst[w] = src[w];
-                unsigned char *buf = smem_raw + b * buf_bytes;
-                if (J->width == 1) stage_tiles<1>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
-                else stage_tiles<2>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
-                asm volatile("cp.async.wait_all;" ::: "memory");
-            } else {
-                const unsigned *src = reinterpret_cast<const unsigned *>(&J->ba);
-                unsigned *dst = reinterpret_cast<unsigned *>(&s_ba[b]);
-                for (int w = lane; w < (int)(sizeof(BlasArgs) / 4); w += PT) dst[w] = src[w];
-            }
-            if (lane == 0) s_it[b] = it;
-            __threadfence_block();
-            bar_arrive(BAR_FULL + b);
-        }
-        return;
-    }
-
-    // ------------------------------------------------------------------- compute warps
-    for (unsigned k = 0;; ++k) {
-        const int b = k & 1;
-        bar_sync(BAR_FULL + b);
-        const unsigned it = s_it[b];
-        if (it >= n_items) break;
-        const ItemDev item = items[it];
-        const JobDev *J = jobs + item.job;
-        const int kind = J->kind;
-        unsigned char *buf = smem_raw + b * buf_bytes;
-        if (kind == JK_NTT) {
-            const int L = J->L[item.pass];
-            if (J->width == 1) {
-                if (J->inv) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
-                else compute_store<1, false>(L, s_pa[b], item.first, buf, tid);
-            } else {
-                if (J->inv) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
-                else compute_store<2, false>(L, s_pa[b], item.first, buf, tid);
-            }
-        } else {
-            const BlasArgs &ba = s_ba[b];
-            const unsigned long long begin = item.first * J->chunk;
-            const unsigned long long end = begin + J->chunk < ba.n ? begin + J->chunk : ba.n;
-            if (J->width == 1) run_blas<1>(J->op, ba, begin, end, tid);
-            else run_blas<2>(J->op, ba, begin, end, tid);
-            ntt_detail::tile_sync<BAR_COMPUTE, BT>();
-        }
-        // every compute thread's stores precede the barrier above; thread 0's release makes them
-        // visible (cumulatively) to whoever acquires the counters
-        if (tid == 0) {
-            __threadfence();
-            if (kind == JK_NTT && J->twopass && item.pass == 0) atomicAdd(poly_ctr + J->poly_base + item.poly, 1u);
-            atomicAdd(job_ctr + item.job, 1u);
-        }
-        __threadfence_block();
-        bar_arrive(BAR_EMPTY + b);
-    }
-}
-
-size_t kernel_smem() {
-    size_t m = 0;
-    m = std::max(m, Shape<2, 6>::SMEM);
-    m = std::max(m, Shape<2, 7>::SMEM);
-    m = std::max(m, Shape<2, 8>::SMEM);
-    m = std::max(m, Shape<2, 9>::SMEM);
-    m = std::max(m, Shape<2, 10>::SMEM);
-    m = std::max(m, Shape<2, 11>::SMEM);
-    return m;
-}
 
 // tiles of 2^L residues per CTA of 256 threads (the Shape rule for L <= 11)
 inline unsigned tiles_per_cta(int L) { return 1u << (11 - L); }
@@ -337,6 +72,8 @@ struct mq_batch {
     unsigned *dctrs = nullptr;
     size_t n_ctrs = 0;
     size_t n_items = 0, ntt_items = 0, blas_items = 0;
+    int variant = 3;  // kernel instantiation (job_variant)
+    int form = 0;     // kernel form (kernel_form)
     unsigned grid = 0;
     size_t smem = 0;
     unsigned long long limit_ns = 0;
@@ -623,33 +360,78 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
     out.items.resize(keys.size());
     for (size_t k = 0; k < keys.size(); ++k) out.items[k] = keys[k].it;
     out.n_ctrs = 2 + njobs + poly_ctrs;
+    out.variant = job_variant(jobs, njobs);
     return MQ_OK;
 }
 
-int mq::batch_detail::persistent_grid(unsigned ctas_per_sm, unsigned *grid, size_t *smem) {
+// the instantiations: 0 the general one (any mix), 1 64-bit transforms only, 2 128-bit transforms only
+static int kernel_slot(int variant) { return variant == 1 ? 1 : variant == 2 ? 2 : 0; }
+
+int mq::batch_detail::job_variant(const mq_job *jobs, size_t njobs) {
+    int v = 0;
+    for (size_t i = 0; i < njobs; ++i) {
+        const bool ntt = is_ntt(jobs[i].kind);
+        const int w = ntt ? (jobs[i].plan ? jobs[i].plan->width : 2) : jobs[i].width;
+        v |= (w == MQ_W64 ? 1 : 2) | (ntt ? 0 : 4);
+    }
+    return v ? v : 3;
+}
+
+int mq::batch_detail::kernel_form(int variant, unsigned flags) {
+    if (flags & MQ_BATCH_FORM_PREFETCH) return 1;
+    if (flags & MQ_BATCH_FORM_SPLIT) return 0;
+    (void)variant;  // the prefetching form measured faster for every instantiation
+    return 1;
+}
+
+int mq::batch_detail::persistent_grid(int variant, int form, unsigned ctas_per_sm, unsigned *grid, size_t *smem) {
+    // every instantiation gets its shared-memory limit and occupancy once per process
     static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int per_sm[2][3] = {};
+    static size_t buf[2][3] = {};
+    static const int max_ctas[2][3] = {
+        {PersistentKernel<0, 3, true>::MAXB, PersistentKernel<0, 1, false>::MAXB, PersistentKernel<0, 2, false>::MAXB},
+        {PersistentKernel<1, 3, true>::MAXB, PersistentKernel<1, 1, false>::MAXB, PersistentKernel<1, 2, false>::MAXB}};
     std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * kernel_smem()));
+        cudaError_t e[6] = {PersistentKernel<0, 3, true>::configure(&per_sm[0][0], &buf[0][0]),
+                            PersistentKernel<0, 1, false>::configure(&per_sm[0][1], &buf[0][1]),
+                            PersistentKernel<0, 2, false>::configure(&per_sm[0][2], &buf[0][2]),
+                            PersistentKernel<1, 3, true>::configure(&per_sm[1][0], &buf[1][0]),
+                            PersistentKernel<1, 1, false>::configure(&per_sm[1][1], &buf[1][1]),
+                            PersistentKernel<1, 2, false>::configure(&per_sm[1][2], &buf[1][2])};
+        for (cudaError_t x : e)
+            if (x != cudaSuccess && attr_err == cudaSuccess) attr_err = x;
     });
-    int dev = 0, sms = 0, per_sm = 0;
+    const int k = kernel_slot(variant), f = form ? 1 : 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, CT, 2 * kernel_smem());
-    if (e != cudaSuccess || per_sm < 1) return mq_fail(MQ_ERR_CUDA, "the persistent kernel does not fit on an SM");
-    unsigned want = ctas_per_sm ? ctas_per_sm : 2;
-    *grid = (unsigned)sms * std::min<unsigned>(want, (unsigned)per_sm);
-    *smem = kernel_smem();
+    if (attr_err != cudaSuccess || per_sm[f][k] < 1)
+        return mq_fail(MQ_ERR_CUDA, "the persistent kernel does not fit on an SM");
+    const unsigned fit = std::min<unsigned>((unsigned)per_sm[f][k], (unsigned)max_ctas[f][k]);
+    *grid = (unsigned)sms * (ctas_per_sm ? std::min(ctas_per_sm, fit) : fit);
+    *smem = buf[f][k];
     return MQ_OK;
 }
 
-cudaError_t mq::batch_detail::launch_persistent(const JobDev *djobs, const ItemDev *ditems, unsigned n_items,
-                                                unsigned *dctrs, size_t n_ctrs, unsigned njobs,
+cudaError_t mq::batch_detail::launch_persistent(int variant, int form, const JobDev *djobs, const ItemDev *ditems,
+                                                unsigned n_items, unsigned *dctrs, size_t n_ctrs, unsigned njobs,
                                                 unsigned long long limit_ns, unsigned grid, size_t smem,
                                                 cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(dctrs, 0, n_ctrs * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    persistent_kernel<<<grid, CT, 2 * smem, s>>>(djobs, ditems, n_items, dctrs, njobs, limit_ns, smem);
-    return cudaGetLastError();
+    const int k = kernel_slot(variant);
+#define MQ_LAUNCH(F, WM, BL) return PersistentKernel<F, WM, BL>::launch(djobs, ditems, n_items, dctrs, njobs, limit_ns, grid, smem, s)
+    if (form) {
+        if (k == 2) MQ_LAUNCH(1, 2, false);
+        if (k == 1) MQ_LAUNCH(1, 1, false);
+        MQ_LAUNCH(1, 3, true);
+    }
+    if (k == 2) MQ_LAUNCH(0, 2, false);
+    if (k == 1) MQ_LAUNCH(0, 1, false);
+    MQ_LAUNCH(0, 3, true);
+#undef MQ_LAUNCH
 }
 
 static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o);
@@ -673,7 +455,7 @@ static void destroy_batch(mq_batch *b) {
 }
 
 static int enqueue_run(mq_batch *b, cudaStream_t s) {
-    cudaError_t e = launch_persistent(b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
+    cudaError_t e = launch_persistent(b->variant, b->form, b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
                                       (unsigned)b->hjobs.size(), b->limit_ns, b->grid, b->smem, s);
     if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
     e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -697,7 +479,9 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
     apply_defaults(b->opts);
     b->limit_ns = (unsigned long long)(b->opts.wait_timeout_s * 1e9);
     b->scratch.assign(njobs, nullptr);
-    int rc = persistent_grid(b->opts.ctas_per_sm, &b->grid, &b->smem);
+    b->variant = job_variant(jobs, njobs);
+    b->form = kernel_form(b->variant, b->opts.flags);
+    int rc = persistent_grid(b->variant, b->form, b->opts.ctas_per_sm, &b->grid, &b->smem);
     if (rc) {
         destroy_batch(b);
         return rc;
@@ -885,12 +669,15 @@ static bool cache_get(const char *path, const std::string &key, mq_batch_opts &o
     std::string s = read_file(path);
     size_t at = s.find("\"" + key + "\"");
     if (at == std::string::npos) return false;
-    unsigned c = 0, l = 0, bc = 0;
-    if (sscanf(s.c_str() + at + key.size() + 2, " : {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u", &c, &l, &bc) != 3)
-        return false;
+    unsigned c = 0, l = 0, bc = 0, form = 1;
+    const int got = sscanf(s.c_str() + at + key.size() + 2,
+                           " : {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %u", &c, &l, &bc, &form);
+    if (got < 3) return false;
     o.ctas_per_sm = c;
     o.lag = l;
     o.blas_chunk = bc;
+    o.flags = (o.flags & ~(MQ_BATCH_FORM_SPLIT | MQ_BATCH_FORM_PREFETCH)) |
+              (form ? MQ_BATCH_FORM_PREFETCH : MQ_BATCH_FORM_SPLIT);
     return true;
 }
 
@@ -907,8 +694,8 @@ static void cache_put(const char *path, const std::string &key, const mq_batch_o
         pos = end;
     }
     char buf[512];
-    snprintf(buf, sizeof buf, "\"%s\": {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"ms\": %.4f}", key.c_str(),
-             o.ctas_per_sm, o.lag, o.blas_chunk, ms);
+    snprintf(buf, sizeof buf, "\"%s\": {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %d, \"ms\": %.4f}",
+             key.c_str(), o.ctas_per_sm, o.lag, o.blas_chunk, (o.flags & MQ_BATCH_FORM_SPLIT) ? 0 : 1, ms);
     entries.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "wb");
@@ -934,7 +721,8 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
         has_blas |= !is_ntt(jobs[i].kind);
         has_deps |= jobs[i].after >= 0 || (is_ntt(jobs[i].kind) && jobs[i].plan && jobs[i].plan->log2n > LMAX);
     }
-    const unsigned ctas[] = {1, 2};
+    const unsigned forms[] = {MQ_BATCH_FORM_PREFETCH, MQ_BATCH_FORM_SPLIT};
+    const unsigned ctas[] = {1, 2, 3};
     const unsigned lags[] = {1, 2, 4, 8};
     const unsigned chunks[] = {8192, 16384, 65536};
     double best_ms = 1e30;
@@ -943,37 +731,48 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     int rc = MQ_OK;
-    for (unsigned c : ctas)
-        for (unsigned l : lags) {
-            if (!has_deps && l != 2) continue;
-            for (unsigned ch : chunks) {
-                if (!has_blas && ch != 16384) continue;
-                mq_batch_opts o{};
-                o.ctas_per_sm = c;
-                o.lag = l;
-                o.blas_chunk = ch;
-                mq_batch *b = nullptr;
-                rc = mq_batch_create(&b, jobs, njobs, &o, stream);
-                if (rc) goto done;
-                float ms = 0, sum = 0;
-                for (int r = 0; r < 2; ++r) mq_batch_launch(b, stream);  // warm-up
-                for (int r = 0; r < 5; ++r) {
-                    cudaEventRecord(t0, s);
-                    mq_batch_launch(b, stream);
-                    cudaEventRecord(t1, s);
-                    cudaEventSynchronize(t1);
-                    cudaEventElapsedTime(&ms, t0, t1);
-                    sum += ms;
-                }
-                rc = mq_batch_status(b);
-                mq_batch_destroy(b);
-                if (rc) goto done;
-                if (sum / 5 < best_ms) {
-                    best_ms = sum / 5;
-                    bo = o;
+    for (unsigned fm : forms) {
+        unsigned last_grid = 0;
+        for (unsigned c : ctas) {
+            unsigned grid = 0;
+            size_t smem = 0;
+            rc = persistent_grid(job_variant(jobs, njobs), fm == MQ_BATCH_FORM_PREFETCH, c, &grid, &smem);
+            if (rc) goto done;
+            if (grid == last_grid) continue;  // more CTAs per SM than this instantiation holds
+            last_grid = grid;
+            for (unsigned l : lags) {
+                if (!has_deps && l != 2) continue;
+                for (unsigned ch : chunks) {
+                    if (!has_blas && ch != 16384) continue;
+                    mq_batch_opts o{};
+                    o.ctas_per_sm = c;
+                    o.lag = l;
+                    o.blas_chunk = ch;
+                    o.flags = fm;
+                    mq_batch *b = nullptr;
+                    rc = mq_batch_create(&b, jobs, njobs, &o, stream);
+                    if (rc) goto done;
+                    float ms = 0, sum = 0;
+                    for (int r = 0; r < 2; ++r) mq_batch_launch(b, stream);  // warm-up
+                    for (int r = 0; r < 5; ++r) {
+                        cudaEventRecord(t0, s);
+                        mq_batch_launch(b, stream);
+                        cudaEventRecord(t1, s);
+                        cudaEventSynchronize(t1);
+                        cudaEventElapsedTime(&ms, t0, t1);
+                        sum += ms;
+                    }
+                    rc = mq_batch_status(b);
+                    mq_batch_destroy(b);
+                    if (rc) goto done;
+                    if (sum / 5 < best_ms) {
+                        best_ms = sum / 5;
+                        bo = o;
+                    }
                 }
             }
         }
+    }
     *best = bo;
     apply_defaults(*best);
     if (cache_path && *cache_path) cache_put(cache_path, shape_key(std::vector<mq_job>(jobs, jobs + njobs)), *best, best_ms);

@@ -44,6 +44,7 @@ struct BatchTables {
     std::vector<ItemDev> items;
     size_t n_ctrs = 0;        // counters to zero before each launch
     size_t ntt_items = 0, blas_items = 0;
+    int variant = 3;          // kernel instantiation (job_variant)
 };
 
 // Staging bytes a job needs (natural-order transforms in two passes), 0 if none.
@@ -62,14 +63,23 @@ int check_job(const mq_job &j, const mq_batch_opts &opts);
 int refill_jobs(const mq_job *jobs, size_t njobs, const mq_batch_opts &opts, void *const *scratch,
                 std::vector<JobDev> &jobs_io);
 
-// Persistent CTAs for `ctas_per_sm` (0: as many as fit, at most 2) on the current device, and the
-// dynamic shared memory of a launch.
-int persistent_grid(unsigned ctas_per_sm, unsigned *grid, size_t *smem);
+// Which persistent kernel instantiation covers the jobs: residue widths present (bit 0: 64-bit,
+// bit 1: 128-bit) | 4 if any BLAS job.
+int job_variant(const mq_job *jobs, size_t njobs);
 
-// Zero the counters and launch the persistent kernel on `s` (asynchronous).
-cudaError_t launch_persistent(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, unsigned *dctrs,
-                              size_t n_ctrs, unsigned njobs, unsigned long long limit_ns, unsigned grid, size_t smem,
-                              cudaStream_t s);
+// Kernel form for a batch: 0 warp-specialised, 1 prefetching (MQ_BATCH_FORM_* flags, else the
+// default for the variant).
+int kernel_form(int variant, unsigned flags);
+
+// Persistent CTAs of the instantiation for `variant` and `form` with `ctas_per_sm` (0: as many as
+// fit) on the current device, and the bytes of one tile buffer.
+int persistent_grid(int variant, int form, unsigned ctas_per_sm, unsigned *grid, size_t *smem);
+
+// Zero the counters and launch the persistent kernel instantiation that covers `variant` (the
+// tables' variant) on `s` (asynchronous).
+cudaError_t launch_persistent(int variant, int form, const JobDev *djobs, const ItemDev *ditems, unsigned n_items,
+                              unsigned *dctrs, size_t n_ctrs, unsigned njobs, unsigned long long limit_ns,
+                              unsigned grid, size_t smem, cudaStream_t s);
 
 void apply_defaults(mq_batch_opts &o);
 

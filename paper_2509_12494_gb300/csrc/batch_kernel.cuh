@@ -1,0 +1,471 @@
+// batch_kernel.cuh -- the warp-specialised persistent kernel of the batched form, as a template
+// over the residue widths and job kinds it carries (instantiated in batch_k_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "batch_internal.h"
+#include "blas_ops.cuh"
+#include "common.cuh"
+#include "ntt_kernel.cuh"
+
+namespace mq {
+namespace batch_detail {
+
+using ntt_detail::Shape;
+using ntt_detail::Traits;
+
+constexpr int BT = 256;               // threads per persistent CTA
+constexpr int LMIN = 6, LMAX = 11;    // tile sizes the persistent kernel carries
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_status(const unsigned *p) {
+    return (int)*(const volatile unsigned *)p;
+}
+
+// Bounded wait until *ctr >= target.  Returns false on timeout or when the batch already failed.
+static __device__ __noinline__ bool wait_geq(const unsigned *ctr, unsigned target, const unsigned *status, unsigned long long limit_ns) {
+    if (ld_acquire(ctr) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        __nanosleep(200);
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_status(status) != 0) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ uint4 u4(const uint64_t v[2]) {
+    return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
+}
+
+// residues [begin, end) of a BLAS job; 16-byte aligned operands (checked on the host)
+template <int W, int OP>
+__device__ __forceinline__ void blas_chunk(const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
+    if (W == 2) {
+        const Mod128 m{u4(b.q), u4(b.mu), b.L};
+        const uint4 s = u4(b.s), sp = u4(b.sp);
+        const uint4 *A = reinterpret_cast<const uint4 *>(b.a), *B = reinterpret_cast<const uint4 *>(b.b);
+        uint4 *C = reinterpret_cast<uint4 *>(b.c);
+        // one residue per thread and step: the wave of resident CTAs keeps enough loads in flight,
+        // and an unrolled Barrett would spill inside this many-branched kernel
+        for (unsigned long long i = begin + tid; i < end; i += BT) {
+            const uint4 va = __ldcg(A + i), vb = __ldcg(B + i);
+            __stcg(C + i, op128<OP>(va, vb, m, s, sp));
+        }
+    } else {
+        const Mod64 m{b.q[0], b.mu[0], b.L};
+        const uint64_t s = b.s[0], sp = b.sp[0];
+        // begin is a multiple of the (even) chunk: pairs first, then a possible odd last residue
+        const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(b.a), *B = reinterpret_cast<const ulonglong2 *>(b.b);
+        ulonglong2 *C = reinterpret_cast<ulonglong2 *>(b.c);
+        const unsigned long long vb0 = begin / 2, ve = end / 2;
+        for (unsigned long long i = vb0 + tid; i < ve; i += BT) {
+            ulonglong2 x = __ldcg(A + i), y = __ldcg(B + i), r;
+            r.x = op64<OP>(x.x, y.x, m, s, sp);
+            r.y = op64<OP>(x.y, y.y, m, s, sp);
+            __stcg(C + i, r);
+        }
+        if ((end & 1) && tid == 0) {
+            const unsigned long long *a1 = reinterpret_cast<const unsigned long long *>(b.a);
+            const unsigned long long *b1 = reinterpret_cast<const unsigned long long *>(b.b);
+            unsigned long long *c1 = reinterpret_cast<unsigned long long *>(b.c);
+            c1[end - 1] = op64<OP>(__ldcg(a1 + end - 1), __ldcg(b1 + end - 1), m, s, sp);
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void run_blas(int op, const BlasArgs &b, unsigned long long begin, unsigned long long end, int tid) {
+    switch (op) {
+    case OP_VADD: blas_chunk<W, OP_VADD>(b, begin, end, tid); break;
+    case OP_VSUB: blas_chunk<W, OP_VSUB>(b, begin, end, tid); break;
+    case OP_VMUL: blas_chunk<W, OP_VMUL>(b, begin, end, tid); break;
+    default: blas_chunk<W, OP_AXPY>(b, begin, end, tid); break;
+    }
+}
+
+constexpr int PT = 64;              // producer threads (two warps)
+constexpr int CT = BT + PT;         // threads per persistent CTA
+constexpr int BAR_COMPUTE = 1;      // named barrier of the BT compute threads
+constexpr int BAR_FULL = 2;         // + buffer: producer -> compute, "buffer b holds item k"
+constexpr int BAR_EMPTY = 4;        // + buffer: compute -> producer, "buffer b is free again"
+constexpr int BAR_PRODUCER = 6;     // named barrier of the PT producer threads
+
+// named barriers with immediate ids (a register id would make ptxas reserve all sixteen)
+__device__ __forceinline__ void bar_arrive(int id) {
+    if (id == BAR_FULL) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
+    else if (id == BAR_FULL + 1) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
+    else if (id == BAR_EMPTY) asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
+    else asm volatile("bar.arrive %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id) {
+    if (id == BAR_FULL) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL), "n"(CT) : "memory");
+    else if (id == BAR_FULL + 1) asm volatile("bar.sync %0, %1;" ::"n"(BAR_FULL + 1), "n"(CT) : "memory");
+    else if (id == BAR_EMPTY) asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY), "n"(CT) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR_EMPTY + 1), "n"(CT) : "memory");
+}
+
+// Stage an item's tiles: cp.async for 128-bit residues (16-byte copies through L2).  64-bit
+// residues take 8-byte copies, which also allocate in the SM's L1; those are used only where
+// ASYNC64 is set, by the prefetching form, whose every dependency is taken with an acquire load
+// at GPU scope before the copies start (an acquire orders the later weak loads of the CTA after
+// the producer's release whatever their cache operator, so no stale L1 line can be read).  The
+// split form stages 64-bit tiles with batched L2 loads.
+template <int W, int NTH = PT, bool ASYNC64 = false>
+__device__ __forceinline__ void stage_tiles(int L, const PassArgs &a, unsigned long long first, void *sm, int lane) {
+    typedef typename Traits<W>::E E;
+    E *s = reinterpret_cast<E *>(sm);
+#define MQ_STAGE(LL)                                                                      \
+    if (W == 2 || ASYNC64) ntt_detail::load_tiles_async<W, LL, NTH>(a, first, s, lane);   \
+    else ntt_detail::load_tiles_sync<W, LL, NTH>(a, first, s, lane);                       \
+    break;
+    switch (L) {
+    case 6: MQ_STAGE(6)
+    case 7: MQ_STAGE(7)
+    case 8: MQ_STAGE(8)
+    case 9: MQ_STAGE(9)
+    case 10: MQ_STAGE(10)
+    default: MQ_STAGE(11)
+    }
+#undef MQ_STAGE
+}
+
+template <int W, bool INV>
+__device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned long long first, void *sm, int tid) {
+    typedef typename Traits<W>::E E;
+    E *s = reinterpret_cast<E *>(sm);
+    switch (L) {
+    case 6: ntt_detail::tile_compute_store<W, 6, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 7: ntt_detail::tile_compute_store<W, 7, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 8: ntt_detail::tile_compute_store<W, 8, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 9: ntt_detail::tile_compute_store<W, 9, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    case 10: ntt_detail::tile_compute_store<W, 10, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    default: ntt_detail::tile_compute_store<W, 11, INV, BAR_COMPUTE>(a, first, s, tid); break;
+    }
+}
+
+// ctrs: [0] next item, [1] status, [2, 2 + njobs) per-job finished items, then per-polynomial
+// finished first-pass items of two-pass transforms.
+//
+// Warp-specialised: warps 8-9 are the producer.  For item k it waits until buffer k % 2 is free,
+// takes the next item index, waits (bounded) for the item's dependencies, copies its arguments
+// and stages its tiles into the buffer, and hands it over.  Warps 0-7 compute and store the item,
+// publish its completion on the counters, and free the buffer.  The producer therefore runs one
+// item ahead, and its waits and loads overlap the transform of the previous item.
+// WM: residue widths present (bit 0: 64-bit, bit 1: 128-bit); BL: BLAS jobs present.  A batch runs
+// the narrowest instantiation that covers its jobs, which keeps registers and code small.  64-bit
+// transforms alone need fewer registers and half the shared memory, and their arithmetic has
+// shorter dependency chains per residue, so that instantiation runs three CTAs per SM to keep more
+// warps in flight.
+template <int WM, bool BL>
+struct KCfg {
+    static constexpr int MINB = (WM == 1 && !BL) ? 3 : 2;  // resident CTAs per SM the registers allow
+    static constexpr int W = (WM & 2) ? 2 : 1;              // widest residue (sizes the tile buffers)
+};
+
+template <int WM, bool BL>
+__global__ void __launch_bounds__(CT, KCfg<WM, BL>::MINB)
+    persistent_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
+                      unsigned *ctrs, unsigned njobs, unsigned long long limit_ns, size_t buf_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PassArgs s_pa[2];
+    __shared__ BlasArgs s_ba[2];
+    __shared__ unsigned s_it[2];
+    __shared__ unsigned s_pit;
+    __shared__ int s_pok;
+    const int tid = threadIdx.x;
+    unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
+
+    if (tid >= BT) {  // ----------------------------------------------- producer warps
+        const int lane = tid - BT;  // 0 .. PT-1
+        for (unsigned k = 0;; ++k) {
+            const int b = k & 1;
+            if (k >= 2) bar_sync(BAR_EMPTY + b);
+            if (lane == 0) {
+                unsigned it0 = atomicAdd(ctrs, 1u);
+                if (ld_status(status) != 0) it0 = n_items;  // the batch failed: drain
+                int w = it0 < n_items;
+                if (w) {
+                    const ItemDev i0 = items[it0];
+                    const JobDev *J0 = jobs + i0.job;
+                    if (J0->kind == JK_NTT && J0->twopass && i0.pass == 1)
+                        w = wait_geq(poly_ctr + J0->poly_base + i0.poly, J0->groups0, status, limit_ns);
+                    else if (i0.pass == 0 && J0->after >= 0)
+                        w = wait_geq(job_ctr + J0->after, jobs[J0->after].n_items, status, limit_ns);
+                    if (!w) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
+                }
+                s_pit = it0;
+                s_pok = w;
+            }
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");
+            const unsigned it = s_pit;
+            const bool ok = s_pok != 0;
+            asm volatile("bar.sync %0, %1;" ::"n"(BAR_PRODUCER), "n"(PT) : "memory");  // s_pit reusable
+            ItemDev item;
+            const JobDev *J = jobs;
+            if (ok) {
+                item = items[it];
+                J = jobs + item.job;
+            }
+            if (!ok) {  // end of the work (or a failed wait): tell the compute warps and stop
+                if (lane == 0) s_it[b] = n_items;
+                __threadfence_block();
+                bar_arrive(BAR_FULL + b);
+                break;
+            }
+            if (!BL || J->kind == JK_NTT) {
+                const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
+                unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
+                for (int w = lane; w < (int)(sizeof(PassArgs) / 4); w += PT) dst[w] = src[w];
+                unsigned char *buf = smem_raw + b * buf_bytes;
+                if ((WM & 1) && (!(WM & 2) || J->width == 1))
+                    stage_tiles<1>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
+                else if (WM & 2)
+                    stage_tiles<2>(J->L[item.pass], J->pa[item.pass], item.first, buf, lane);
+                asm volatile("cp.async.wait_all;" ::: "memory");
+            } else {
+                const unsigned *src = reinterpret_cast<const unsigned *>(&J->ba);
+                unsigned *dst = reinterpret_cast<unsigned *>(&s_ba[b]);
+                for (int w = lane; w < (int)(sizeof(BlasArgs) / 4); w += PT) dst[w] = src[w];
+            }
+            if (lane == 0) s_it[b] = it;
+            __threadfence_block();
+            bar_arrive(BAR_FULL + b);
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------------- compute warps
+    for (unsigned k = 0;; ++k) {
+        const int b = k & 1;
+        bar_sync(BAR_FULL + b);
+        const unsigned it = s_it[b];
+        if (it >= n_items) break;
+        const ItemDev item = items[it];
+        const JobDev *J = jobs + item.job;
+        const int kind = J->kind;
+        unsigned char *buf = smem_raw + b * buf_bytes;
+        if (!BL || kind == JK_NTT) {
+            const int L = J->L[item.pass];
+            if ((WM & 1) && (!(WM & 2) || J->width == 1)) {
+                if (J->inv) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<1, false>(L, s_pa[b], item.first, buf, tid);
+            } else if (WM & 2) {
+                if (J->inv) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<2, false>(L, s_pa[b], item.first, buf, tid);
+            }
+        } else if (BL) {
+            const BlasArgs &ba = s_ba[b];
+            const unsigned long long begin = item.first * J->chunk;
+            const unsigned long long end = begin + J->chunk < ba.n ? begin + J->chunk : ba.n;
+            if ((WM & 1) && (!(WM & 2) || J->width == 1)) run_blas<1>(J->op, ba, begin, end, tid);
+            else if (WM & 2) run_blas<2>(J->op, ba, begin, end, tid);
+            ntt_detail::tile_sync<BAR_COMPUTE, BT>();
+        }
+        // every compute thread's stores precede the barrier above; thread 0's release makes them
+        // visible (cumulatively) to whoever acquires the counters
+        if (tid == 0) {
+            __threadfence();
+            if ((!BL || kind == JK_NTT) && J->twopass && item.pass == 0) atomicAdd(poly_ctr + J->poly_base + item.poly, 1u);
+            atomicAdd(job_ctr + item.job, 1u);
+        }
+        __threadfence_block();
+        bar_arrive(BAR_EMPTY + b);
+    }
+}
+
+// The prefetching form: all BT threads compute, and each CTA prefetches its next item while it
+// transforms the current one (the per-call pass kernel's double buffering, with items from the
+// work list).  Thread 0 takes the next item index and checks, without waiting, whether its
+// dependencies are met; if so the CTA starts its copies (cp.async through L2 for 128-bit tiles)
+// before the transform, else after it, once a bounded wait ended.  No warps are set aside for
+// staging, so every thread keeps the register budget of the per-call kernel (three CTAs per SM).
+template <int WM, bool BL>
+__global__ void __launch_bounds__(BT, 3)
+    prefetch_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
+                    unsigned *ctrs, unsigned njobs, unsigned long long limit_ns, size_t buf_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PassArgs s_pa[2];
+    __shared__ BlasArgs s_ba[2];
+    __shared__ unsigned s_it[2];
+    __shared__ int s_ready;
+    const int tid = threadIdx.x;
+    unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
+
+    // thread 0: the counter an item waits on and its target (none: target 0)
+    auto dep_of = [&](unsigned it, const unsigned **ctr, unsigned *target) {
+        const ItemDev i0 = items[it];
+        const JobDev *J0 = jobs + i0.job;
+        *target = 0;
+        if ((!BL || J0->kind == JK_NTT) && J0->twopass && i0.pass == 1) {
+            *ctr = poly_ctr + J0->poly_base + i0.poly;
+            *target = J0->groups0;
+        } else if (i0.pass == 0 && J0->after >= 0) {
+            *ctr = job_ctr + J0->after;
+            *target = jobs[J0->after].n_items;
+        }
+    };
+    // thread 0: take an item for buffer b; s_ready = its dependencies are met now (or nothing to do)
+    auto fetch = [&](int b) {
+        unsigned it = atomicAdd(ctrs, 1u);
+        if (ld_status(status) != 0) it = n_items;  // the batch failed: drain
+        int ready = 1;
+        if (it < n_items) {
+            const unsigned *c = nullptr;
+            unsigned target = 0;
+            dep_of(it, &c, &target);
+            if (target) ready = ld_acquire(c) >= target;
+        }
+        s_it[b] = it;
+        s_ready = ready;
+    };
+    // all threads: copy the item's arguments and start staging its tiles into buffer b
+    auto stage = [&](int b, unsigned it) {
+        const ItemDev item = items[it];
+        const JobDev *J = jobs + item.job;
+        if (!BL || J->kind == JK_NTT) {
+            const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
+            unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
+            for (int w = tid; w < (int)(sizeof(PassArgs) / 4); w += BT) dst[w] = src[w];
+            unsigned char *buf = smem_raw + b * buf_bytes;
+            if ((WM & 1) && (!(WM & 2) || J->width == 1))
+                stage_tiles<1, BT, true>(J->L[item.pass], J->pa[item.pass], item.first, buf, tid);
+            else if (WM & 2)
+                stage_tiles<2, BT>(J->L[item.pass], J->pa[item.pass], item.first, buf, tid);
+        } else {
+            const unsigned *src = reinterpret_cast<const unsigned *>(&J->ba);
+            unsigned *dst = reinterpret_cast<unsigned *>(&s_ba[b]);
+            for (int w = tid; w < (int)(sizeof(BlasArgs) / 4); w += BT) dst[w] = src[w];
+        }
+    };
+    // thread 0: bounded wait for the item in buffer b; on timeout the item is dropped
+    auto wait_for = [&](int b) {
+        const unsigned it = s_it[b];
+        const unsigned *c = nullptr;
+        unsigned target = 0;
+        dep_of(it, &c, &target);
+        if (target && !wait_geq(c, target, status, limit_ns)) {
+            atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
+            s_it[b] = n_items;
+        }
+    };
+
+    if (tid == 0) {
+        fetch(0);
+        if (!s_ready) wait_for(0);
+    }
+    __syncthreads();
+    if (s_it[0] < n_items) stage(0, s_it[0]);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    for (unsigned k = 0;; ++k) {
+        const int b = k & 1;
+        const unsigned it = s_it[b];
+        if (it >= n_items) break;
+        if (tid == 0) fetch(b ^ 1);
+        __syncthreads();  // s_it[b ^ 1], s_ready
+        const unsigned nx = s_it[b ^ 1];
+        const bool early = nx < n_items && s_ready;
+        if (early) stage(b ^ 1, nx);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (early) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // every thread's copies of the current item (and its arguments) landed
+
+        const ItemDev item = items[it];
+        const JobDev *J = jobs + item.job;
+        const int kind = J->kind;
+        unsigned char *buf = smem_raw + b * buf_bytes;
+        if (!BL || kind == JK_NTT) {
+            const int L = J->L[item.pass];
+            if ((WM & 1) && (!(WM & 2) || J->width == 1)) {
+                if (J->inv) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<1, false>(L, s_pa[b], item.first, buf, tid);
+            } else if (WM & 2) {
+                if (J->inv) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
+                else compute_store<2, false>(L, s_pa[b], item.first, buf, tid);
+            }
+        } else if (BL) {
+            const BlasArgs &ba = s_ba[b];
+            const unsigned long long begin = item.first * J->chunk;
+            const unsigned long long end = begin + J->chunk < ba.n ? begin + J->chunk : ba.n;
+            if ((WM & 1) && (!(WM & 2) || J->width == 1)) run_blas<1>(J->op, ba, begin, end, tid);
+            else if (WM & 2) run_blas<2>(J->op, ba, begin, end, tid);
+            ntt_detail::tile_sync<BAR_COMPUTE, BT>();
+        }
+        // every thread's stores precede the barrier that ends the item; thread 0's release makes
+        // them visible (cumulatively) to whoever acquires the counters
+        if (tid == 0) {
+            __threadfence();
+            if ((!BL || kind == JK_NTT) && J->twopass && item.pass == 0) atomicAdd(poly_ctr + J->poly_base + item.poly, 1u);
+            atomicAdd(job_ctr + item.job, 1u);
+        }
+        if (nx < n_items && !early) {  // the next item was not ready: wait for it now, then stage it
+            if (tid == 0) wait_for(b ^ 1);
+            __syncthreads();
+            if (s_it[b ^ 1] < n_items) stage(b ^ 1, s_it[b ^ 1]);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Shared memory of one buffer: the largest tile group of width W (every group holds 2048 residues).
+template <int W>
+inline size_t kernel_smem() {
+    size_t m = 0;
+    m = m > Shape<W, 6>::SMEM ? m : Shape<W, 6>::SMEM;
+    m = m > Shape<W, 7>::SMEM ? m : Shape<W, 7>::SMEM;
+    m = m > Shape<W, 8>::SMEM ? m : Shape<W, 8>::SMEM;
+    m = m > Shape<W, 9>::SMEM ? m : Shape<W, 9>::SMEM;
+    m = m > Shape<W, 10>::SMEM ? m : Shape<W, 10>::SMEM;
+    m = m > Shape<W, 11>::SMEM ? m : Shape<W, 11>::SMEM;
+    return (m + 15) / 16 * 16;
+}
+
+// Launch helpers of one instantiation (defined in batch_k_*.cu).  FORM 0: warp-specialised
+// (persistent_kernel), FORM 1: prefetching (prefetch_kernel).
+template <int FORM, int WM, bool BL>
+struct PersistentKernel {
+    static constexpr int THREADS = FORM ? BT : CT;
+    static constexpr int MAXB = FORM ? 3 : KCfg<WM, BL>::MINB;  // CTAs per SM the registers allow
+    // set the shared-memory limit; *per_sm = resident CTAs per SM, *smem = bytes of one buffer
+    static cudaError_t configure(int *per_sm, size_t *smem);
+    static cudaError_t launch(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, unsigned *dctrs,
+                              unsigned njobs, unsigned long long limit_ns, unsigned grid, size_t smem, cudaStream_t s);
+};
+
+#define MQ_DEFINE_PERSISTENT_FORM(FORM, KERNEL, WM, BL)                                                   \
+    template <>                                                                                            \
+    cudaError_t PersistentKernel<FORM, WM, BL>::configure(int *per_sm, size_t *smem) {                     \
+        *smem = kernel_smem<KCfg<WM, BL>::W>();                                                            \
+        cudaError_t e = cudaFuncSetAttribute(KERNEL<WM, BL>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                             (int)(2 * *smem));                                            \
+        if (e != cudaSuccess) return e;                                                                    \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, KERNEL<WM, BL>, THREADS, 2 * *smem);  \
+    }                                                                                                      \
+    template <>                                                                                            \
+    cudaError_t PersistentKernel<FORM, WM, BL>::launch(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, \
+                                                       unsigned *dctrs, unsigned njobs, unsigned long long limit_ns, \
+                                                       unsigned grid, size_t smem, cudaStream_t s) {           \
+        KERNEL<WM, BL><<<grid, THREADS, 2 * smem, s>>>(djobs, ditems, n_items, dctrs, njobs, limit_ns, smem); \
+        return cudaGetLastError();                                                                         \
+    }
+
+#define MQ_DEFINE_PERSISTENT(WM, BL)                          \
+    MQ_DEFINE_PERSISTENT_FORM(0, persistent_kernel, WM, BL)   \
+    MQ_DEFINE_PERSISTENT_FORM(1, prefetch_kernel, WM, BL)
+
+}  // namespace batch_detail
+}  // namespace mq

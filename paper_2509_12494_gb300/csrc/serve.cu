@@ -211,7 +211,11 @@ int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
         if (b) rc = mq_pool_alloc(&scratch[i], b, sl->stream);
     }
     BatchTables t;
-    if (!rc) rc = build_tables(jobs.data(), n, s->opts, scratch.data(), 2ull * s->grid, t);
+    unsigned grid = 0;
+    size_t smem = 0;
+    const int variant = job_variant(jobs.data(), n), form = kernel_form(variant, s->opts.flags);
+    if (!rc) rc = persistent_grid(variant, form, 0, &grid, &smem);
+    if (!rc) rc = build_tables(jobs.data(), n, s->opts, scratch.data(), 2ull * grid, t);
     if (!rc) rc = grow(sl, n, std::max<size_t>(1, t.items.size()), t.n_ctrs);
     if (!rc) {
         memcpy(sl->hjobs, t.jobs.data(), n * sizeof(JobDev));
@@ -221,8 +225,8 @@ int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
         if ((e = cudaMemcpyAsync(sl->djobs, sl->hjobs, n * sizeof(JobDev), cudaMemcpyHostToDevice, sl->stream)) != cudaSuccess ||
             (e = cudaMemcpyAsync(sl->ditems, sl->hitems, t.items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice,
                                  sl->stream)) != cudaSuccess ||
-            (e = launch_persistent(sl->djobs, sl->ditems, (unsigned)t.items.size(), sl->dctrs, t.n_ctrs, (unsigned)n,
-                                   (unsigned long long)(s->opts.wait_timeout_s * 1e9), s->grid, s->smem,
+            (e = launch_persistent(variant, form, sl->djobs, sl->ditems, (unsigned)t.items.size(), sl->dctrs, t.n_ctrs,
+                                   (unsigned)n, (unsigned long long)(s->opts.wait_timeout_s * 1e9), grid, smem,
                                    sl->stream)) != cudaSuccess ||
             (e = cudaMemcpyAsync(sl->h_status, sl->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, sl->stream)) !=
                 cudaSuccess)
@@ -364,7 +368,7 @@ extern "C" int mq_server_create(mq_server **out, const mq_server_cfg *cfg) {
     if (s->cfg.wait_timeout_s <= 0) s->cfg.wait_timeout_s = 2.0;
     s->opts.wait_timeout_s = s->cfg.wait_timeout_s;
     apply_defaults(s->opts);
-    int rc = persistent_grid(0, &s->grid, &s->smem);
+    int rc = persistent_grid(3, 0, 0, &s->grid, &s->smem);  // the general instantiation must fit
     if (rc) {
         delete s;
         return rc;

@@ -214,6 +214,7 @@ def mq_version() -> str:
 
 MQ_JOB_NTT_FORWARD, MQ_JOB_NTT_INVERSE, MQ_JOB_VADD, MQ_JOB_VSUB, MQ_JOB_VMUL, MQ_JOB_AXPY = 1, 2, 3, 4, 5, 6
 MQ_BATCH_NO_GRAPH, MQ_BATCH_TEST_DROP_ITEM = 1, 2
+MQ_BATCH_FORM_SPLIT, MQ_BATCH_FORM_PREFETCH = 4, 8
 
 
 class mq_job(ctypes.Structure):

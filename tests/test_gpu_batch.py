@@ -94,6 +94,15 @@ class BlasCase:
         return oracle.blas(self.OOPS[self.op], self.a, self.b, self.q, self.width, s=self.s)
 
 
+FORMS = ["split", "prefetch"]
+
+
+def _opts(M, form, **kw):
+    """Batch options selecting a kernel form (both must give identical results)."""
+    flags = kw.pop("flags", 0) | {"split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[form]
+    return M.mq_batch_opts(flags=flags, **kw)
+
+
 def _run(M, jobs, opts=None):
     b = M.mq_batch_create(jobs, opts)
     M.mq_batch_launch(b)
@@ -103,23 +112,26 @@ def _run(M, jobs, opts=None):
 
 @pytest.mark.parametrize("log2n,bits,flags", [(6, 124, 0), (10, 124, 2), (11, 60, 0), (12, 124, 0), (13, 60, 2),
                                               (16, 124, 2), (16, 124, 0), (17, 60, 0), (17, 124, 2)])
-def test_single_job_equals_per_call_and_oracle(mq, pool, log2n, bits, flags):
+@pytest.mark.parametrize("form", FORMS)
+def test_single_job_equals_per_call_and_oracle(mq, pool, log2n, bits, flags, form):
     for inverse in (False, True):
         c = NttCase(mq, log2n, bits, batch=3, flags=flags, inverse=inverse, seed=log2n + bits)
         want = c.per_call()
-        _run(mq, [c.job()])
+        _run(mq, [c.job()], _opts(mq, form))
         got = mq.to_host(c.d)
         assert np.array_equal(got, want)
         c.check_oracle(got, pool)
 
 
-def test_uniform_batch_forward_then_inverse(mq):
+@pytest.mark.parametrize("bits", [124, 60])
+@pytest.mark.parametrize("form", FORMS)
+def test_uniform_batch_forward_then_inverse(mq, bits, form):
     """Independent transforms, each forward job followed by its inverse in the same launch: the
     forward outputs (checked on a copy) equal the per-call path, the round trip restores x."""
     import torch
-    cases = [NttCase(mq, 16, 124, 1, 2, False, 900 + i) for i in range(12)]
+    cases = [NttCase(mq, 16, bits, 1, 2, False, 900 + i) for i in range(12)]
     # forward only, to compare spectra
-    _run(mq, [c.job() for c in cases])
+    _run(mq, [c.job() for c in cases], _opts(mq, form))
     for c in cases:
         assert np.array_equal(mq.to_host(c.d), c.per_call())
     # forward then inverse (job 12 + i waits for job i)
@@ -127,14 +139,15 @@ def test_uniform_batch_forward_then_inverse(mq):
         c.d.copy_(mq.to_device(c.x))
     jobs = [c.job() for c in cases] + [mq.ntt_job(mq.MQ_JOB_NTT_INVERSE, c.plan, c.d, 1, c.N, after=i)
                                       for i, c in enumerate(cases)]
-    b = _run(mq, jobs)
+    b = _run(mq, jobs, _opts(mq, form))
     assert mq.mq_batch_info(b)["ntt_items"] == 24 * 64
     for c in cases:
         assert np.array_equal(mq.to_host(c.d), c.x)
     torch.cuda.synchronize()
 
 
-def test_uneven_mix_of_sizes_widths_orders_and_blas(mq, pool):
+@pytest.mark.parametrize("form", FORMS)
+def test_uneven_mix_of_sizes_widths_orders_and_blas(mq, pool, form):
     """Transforms of 2^6 .. 2^17, both widths and orders, interleaved with all four BLAS ops of
     ragged lengths: every job's result equals its oracle and per-call result."""
     rng = np.random.default_rng(5)
@@ -153,7 +166,7 @@ def test_uneven_mix_of_sizes_widths_orders_and_blas(mq, pool):
             jobs.append(ntt[i].job())
         if i < len(blas):
             jobs.append(blas[i].job())
-    b = _run(mq, jobs, mq.mq_batch_opts(blas_chunk=4096))
+    b = _run(mq, jobs, _opts(mq, form, blas_chunk=4096))
     info = mq.mq_batch_info(b)
     assert info["ntt_items"] > 0 and info["blas_items"] > 0
     for c, want in zip(ntt, wants):
@@ -165,7 +178,8 @@ def test_uneven_mix_of_sizes_widths_orders_and_blas(mq, pool):
 
 
 @pytest.mark.parametrize("log2n,bits", [(10, 124), (12, 60), (13, 124)])
-def test_polynomial_product_chain(mq, log2n, bits):
+@pytest.mark.parametrize("form", FORMS)
+def test_polynomial_product_chain(mq, log2n, bits, form):
     """forward(a), forward(b) -> vmul -> inverse, as one batch with dependencies, equals the
     schoolbook negacyclic product (Sec. 2.3) computed by the oracle."""
     import torch
@@ -182,7 +196,7 @@ def test_polynomial_product_chain(mq, log2n, bits):
     jobs = [mq.ntt_job(1, plan, da), mq.ntt_job(1, plan, db, after=0),
             mq.blas_job(mq.MQ_JOB_VMUL, dc, da, db, N, q, width, after=1),
             mq.ntt_job(2, plan, dc, after=2)]
-    _run(mq, jobs)
+    _run(mq, jobs, _opts(mq, form))
     want = oracle.negacyclic_mul(a, b, log2n, q, width) if log2n <= 12 else None
     got = mq.to_host(dc)
     if want is not None:
@@ -229,14 +243,15 @@ def test_no_graph_mode_matches(mq):
     assert np.array_equal(mq.to_host(c.d), want)
 
 
-def test_bounded_wait_reports_timeout_and_device_stays_usable(mq):
+@pytest.mark.parametrize("form", FORMS)
+def test_bounded_wait_reports_timeout_and_device_stays_usable(mq, form):
     """Fault injection: one first-pass item is left out, so the second pass of that polynomial
     waits for a counter nothing will complete.  The wait gives up after the limit, the batch
     reports MQ_ERR_TIMEOUT, and the device keeps working."""
     import time
     c = NttCase(mq, 16, 124, 2, 2, False, 31)
     dep = BlasCase(mq, "vadd", 4096, 124, 32)
-    opts = mq.mq_batch_opts(wait_timeout_s=0.2, flags=mq.MQ_BATCH_TEST_DROP_ITEM)
+    opts = _opts(mq, form, wait_timeout_s=0.2, flags=mq.MQ_BATCH_TEST_DROP_ITEM)
     b = mq.mq_batch_create([c.job(), dep.job(after=0)], opts)
     t0 = time.time()
     mq.mq_batch_launch(b)
@@ -250,6 +265,34 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(mq):
     want = c2.per_call()
     _run(mq, [c2.job()])
     assert np.array_equal(mq.to_host(c2.d), want)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_instantiation_follows_batch_contents(mq, form):
+    """Split form: 64-bit transforms alone run three persistent CTAs per SM, any batch with 128-bit
+    residues or BLAS two.  Prefetch form: three for every batch.  An explicit ctas_per_sm is clamped
+    to what the instantiation holds.  Each batch's results equal the per-call path's."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    c60 = NttCase(mq, 14, 60, 2, 0, False, 61)
+    c124 = NttCase(mq, 14, 124, 2, 0, True, 62)
+    bl = BlasCase(mq, "vmul", 70001, 60, 63)
+    two = 2 if form == "split" else 3
+    for jobs, ctas, kw in (([c60], 3, {}), ([c124], two, {}), ([c60, c124], two, {}), ([bl], two, {}),
+                           ([c60], 3, {"ctas_per_sm": 7}), ([c124], two, {"ctas_per_sm": 7}),
+                           ([c60], 1, {"ctas_per_sm": 1})):
+        wants = [j.per_call() if isinstance(j, NttCase) else None for j in jobs]
+        for j in jobs:
+            if isinstance(j, NttCase):
+                j.d.copy_(mq.to_device(j.x).view_as(j.d))
+        b = _run(mq, [j.job() for j in jobs], _opts(mq, form, **kw))
+        assert mq.mq_batch_info(b)["ctas"] == sms * ctas
+        for j, w in zip(jobs, wants):
+            if w is not None:
+                assert np.array_equal(mq.to_host(j.d), w)
+            else:
+                assert np.array_equal(mq.to_host(j.dc), j.expect())
+        mq.mq_batch_destroy(b)
 
 
 def test_rejects_bad_jobs(mq):
@@ -268,9 +311,10 @@ def test_autotuner_writes_cache_and_create_uses_it(mq, tmp_path, monkeypatch):
     jobs = [c.job() for c in cases] + [bl.job()]
     cache = str(tmp_path / "tune.json")
     best = mq.mq_autotune_batch(jobs, cache)
-    assert best.ctas_per_sm in (1, 2) and best.lag >= 1 and best.blas_chunk % 2048 == 0
+    assert best.ctas_per_sm in (1, 2, 3) and best.lag >= 1 and best.blas_chunk % 2048 == 0
+    assert bin(best.flags & (mq.MQ_BATCH_FORM_SPLIT | mq.MQ_BATCH_FORM_PREFETCH)).count("1") == 1
     text = open(cache).read()
-    assert '"ctas_per_sm"' in text and '"ms"' in text
+    assert '"ctas_per_sm"' in text and '"form"' in text and '"ms"' in text
     monkeypatch.setenv("MQNTT_TUNE_CACHE", cache)
     b = mq.mq_batch_create(jobs)
     import torch
