@@ -217,9 +217,7 @@ def run_gpu(args, rank, world):
     # the persistent batch: job i = forward of polynomial i, job batch + i = its inverse
     jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
     jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
-    form_flag = {"default": 0, "split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[args.form]
-    opts = (M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm, flags=form_flag)
-            if (args.lag or args.ctas_per_sm or form_flag) else None)
+    opts = batch_opts(M, args)
     pbatch = M.mq_batch_create(jobs, opts, stream=sh)
     pinfo = M.mq_batch_info(pbatch)
 
@@ -377,7 +375,7 @@ def run_gpu(args, rank, world):
     if not args.no_blas:
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
     if not args.no_uneven:
-        out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps)
+        out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args))
 
     out["clocks"] = clocks
     return out
@@ -503,10 +501,18 @@ def uneven_mix(M, torch, dev, seed=4):
     return dict(ntt=ntt, blas=blas, jobs=jobs, butterflies=bfly, blas_modmuls=mm)
 
 
-def bench_uneven(M, torch, dev, stream, flush, steps):
+def batch_opts(M, args):
+    """Options of the persistent batches from the command line (None: the library's defaults)."""
+    form_flag = {"default": 0, "split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[args.form]
+    if not (args.lag or args.ctas_per_sm or form_flag):
+        return None
+    return M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm, flags=form_flag)
+
+
+def bench_uneven(M, torch, dev, stream, flush, steps, opts=None):
     mix = uneven_mix(M, torch, dev)
     sh = stream.cuda_stream
-    b = M.mq_batch_create(mix["jobs"], stream=sh)
+    b = M.mq_batch_create(mix["jobs"], opts, stream=sh)
     info = M.mq_batch_info(b)
 
     def step_batch():

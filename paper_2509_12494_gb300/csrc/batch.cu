@@ -10,9 +10,10 @@
 // Items are ordered by a software-pipelining key: job chains (a job and the jobs that depend on
 // it) are laid out in submission order, chain c starting at position P(c) = the number of
 // first-stage items of the chains before it; an item of stage s (its pass, plus the stages of the
-// jobs before it in its chain) gets the key P(c) + s * D, D = lag x 4 x SMs items (lag waves of
-// the persistent grid, each CTA holding up to two items), so a dependent stage is fetched about
-// D items after its producer and its waits are normally already satisfied.
+// jobs before it in its chain) gets the key P(c) + s * D, D = lag x 2 x CTAs of the persistent
+// grid (lag waves, counting two items per CTA), so a dependent stage is fetched about D items
+// after its producer and its waits are normally already satisfied.  A lag of several waves
+// matters because a CTA of the prefetching form takes its items up to three ahead.
 // Deadlock freedom: an item waits only for items fetched before it; those were fetched by CTAs
 // that are running, whose own waits are again for earlier items, so every wait ends.  Each wait
 // is still bounded (globaltimer) and sets the batch status to MQ_ERR_TIMEOUT when it gives up;
@@ -232,7 +233,7 @@ static bool same_shape(const mq_job &a, const mq_job &b) {
 }
 
 void mq::batch_detail::apply_defaults(mq_batch_opts &o) {
-    if (o.lag == 0) o.lag = 2;
+    if (o.lag == 0) o.lag = 8;
     if (o.blas_chunk == 0) o.blas_chunk = 16384;
     o.blas_chunk = (o.blas_chunk + 2047) / 2048 * 2048;
     if (o.wait_timeout_s <= 0) o.wait_timeout_s = 2.0;
@@ -311,7 +312,7 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
             k.it.job = (unsigned)i;
             k.it.pass = pass;
             k.it.poly = poly;
-            k.it.pad = 0;
+            k.it.dep = k.it.target = k.it.bump = 0;  // resolved once every job's item count is known
             k.it.first = first;
             if (!dropped && is_ntt(j.kind) && d.twopass && pass == 0) {
                 dropped = true;  // fault injection: this item never runs
@@ -358,7 +359,20 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
         return x.chain < y.chain;
     });
     out.items.resize(keys.size());
-    for (size_t k = 0; k < keys.size(); ++k) out.items[k] = keys[k].it;
+    const unsigned poly0 = 2 + (unsigned)njobs;  // first per-polynomial counter
+    for (size_t k = 0; k < keys.size(); ++k) {
+        ItemDev &it = out.items[k];
+        it = keys[k].it;
+        const JobDev &d = out.jobs[it.job];
+        if (d.kind == JK_NTT && d.twopass && it.pass == 1) {  // the polynomial's first pass
+            it.dep = poly0 + d.poly_base + it.poly;
+            it.target = d.groups0;
+        } else if (it.pass == 0 && d.after >= 0) {  // every item of the job it comes after
+            it.dep = 2 + (unsigned)d.after;
+            it.target = out.jobs[d.after].n_items;
+        }
+        if (d.kind == JK_NTT && d.twopass && it.pass == 0) it.bump = poly0 + d.poly_base + it.poly;
+    }
     out.n_ctrs = 2 + njobs + poly_ctrs;
     out.variant = job_variant(jobs, njobs);
     return MQ_OK;

@@ -30,13 +30,20 @@ struct JobDev {
     BlasArgs ba;               // BLAS operands
 };
 
+// One work item (32 bytes; the prefetching kernel copies it into shared memory with two 16-byte
+// copies).  The host resolves its dependency and completion counters, indices into the counter
+// array of a launch: [0] next item, [1] status, [2, 2 + njobs) finished items per job, then
+// finished first-pass items per polynomial of two-pass transforms.
 struct ItemDev {
     unsigned job;
     unsigned pass;
     unsigned poly;
-    unsigned pad;
+    unsigned dep;     // counter this item waits for, 0: none
+    unsigned target;  // value the dependency counter must reach
+    unsigned bump;    // counter to add one to when done besides the job's (first passes), 0: none
     unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
 };
+static_assert(sizeof(ItemDev) == 32, "work items are copied as two 16-byte halves");
 
 // Host-side expansion of a job list into the device tables of one launch.
 struct BatchTables {

@@ -285,12 +285,27 @@ __global__ void __launch_bounds__(CT, KCfg<WM, BL>::MINB)
     }
 }
 
+// Copy a work item's record into shared memory (two 16-byte copies through L2).
+__device__ __forceinline__ void copy_record(ItemDev *dst, const ItemDev *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16), "l"(reinterpret_cast<const char *>(src) + 16)
+                 : "memory");
+}
+
 // The prefetching form: all BT threads compute, and each CTA prefetches its next item while it
 // transforms the current one (the per-call pass kernel's double buffering, with items from the
-// work list).  Thread 0 takes the next item index and checks, without waiting, whether its
-// dependencies are met; if so the CTA starts its copies (cp.async through L2 for 128-bit tiles)
-// before the transform, else after it, once a bounded wait ended.  No warps are set aside for
-// staging, so every thread keeps the register budget of the per-call kernel (three CTAs per SM).
+// work list).  No warps are set aside for staging, so every thread keeps the register budget of
+// the per-call kernel (three CTAs per SM).
+//
+// Thread 0 runs the item bookkeeping ahead of the transform so that its memory round trips
+// overlap the arithmetic: while item k is transformed it already holds the index of item k + 3
+// (an atomicAdd issued one item earlier) and has the record of item k + 2 on its way into
+// shared memory.  Before item k's transform it checks, without waiting, whether item k + 1's
+// dependency counter has reached its target; if so the CTA starts item k + 1's copies before the
+// transform, else after it, once a bounded wait ended.  Items a CTA takes are processed in the
+// order taken and depend only on items taken before them, so every wait ends (the unfinished
+// item of lowest index always has its dependencies done and its CTA working on it).
 template <int WM, bool BL>
 __global__ void __launch_bounds__(BT, 3)
     prefetch_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
@@ -298,41 +313,15 @@ __global__ void __launch_bounds__(BT, 3)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PassArgs s_pa[2];
     __shared__ BlasArgs s_ba[2];
-    __shared__ unsigned s_it[2];
+    __shared__ __align__(16) ItemDev s_rec[3];  // records of items k, k + 1, k + 2 (slot k % 3)
+    __shared__ unsigned s_idx[3];               // their indices (n_items: none)
     __shared__ int s_ready;
     const int tid = threadIdx.x;
-    unsigned *status = ctrs + 1, *job_ctr = ctrs + 2, *poly_ctr = ctrs + 2 + njobs;
+    unsigned *status = ctrs + 1;
+    (void)njobs;
 
-    // thread 0: the counter an item waits on and its target (none: target 0)
-    auto dep_of = [&](unsigned it, const unsigned **ctr, unsigned *target) {
-        const ItemDev i0 = items[it];
-        const JobDev *J0 = jobs + i0.job;
-        *target = 0;
-        if ((!BL || J0->kind == JK_NTT) && J0->twopass && i0.pass == 1) {
-            *ctr = poly_ctr + J0->poly_base + i0.poly;
-            *target = J0->groups0;
-        } else if (i0.pass == 0 && J0->after >= 0) {
-            *ctr = job_ctr + J0->after;
-            *target = jobs[J0->after].n_items;
-        }
-    };
-    // thread 0: take an item for buffer b; s_ready = its dependencies are met now (or nothing to do)
-    auto fetch = [&](int b) {
-        unsigned it = atomicAdd(ctrs, 1u);
-        if (ld_status(status) != 0) it = n_items;  // the batch failed: drain
-        int ready = 1;
-        if (it < n_items) {
-            const unsigned *c = nullptr;
-            unsigned target = 0;
-            dep_of(it, &c, &target);
-            if (target) ready = ld_acquire(c) >= target;
-        }
-        s_it[b] = it;
-        s_ready = ready;
-    };
     // all threads: copy the item's arguments and start staging its tiles into buffer b
-    auto stage = [&](int b, unsigned it) {
-        const ItemDev item = items[it];
+    auto stage = [&](int b, const ItemDev &item) {
         const JobDev *J = jobs + item.job;
         if (!BL || J->kind == JK_NTT) {
             const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
@@ -349,41 +338,56 @@ __global__ void __launch_bounds__(BT, 3)
             for (int w = tid; w < (int)(sizeof(BlasArgs) / 4); w += BT) dst[w] = src[w];
         }
     };
-    // thread 0: bounded wait for the item in buffer b; on timeout the item is dropped
-    auto wait_for = [&](int b) {
-        const unsigned it = s_it[b];
-        const unsigned *c = nullptr;
-        unsigned target = 0;
-        dep_of(it, &c, &target);
-        if (target && !wait_geq(c, target, status, limit_ns)) {
+    // thread 0: bounded wait for the dependency of the item in slot r; on timeout it is dropped
+    auto wait_for = [&](int r) {
+        const ItemDev &it = s_rec[r];
+        if (it.dep && !wait_geq(ctrs + it.dep, it.target, status, limit_ns)) {
             atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
-            s_it[b] = n_items;
+            s_idx[r] = n_items;
         }
     };
 
+    unsigned pend = 0;  // thread 0: index of the item after the two whose records are in flight
     if (tid == 0) {
-        fetch(0);
-        if (!s_ready) wait_for(0);
+        const unsigned i0 = atomicAdd(ctrs, 1u), i1 = atomicAdd(ctrs, 1u);
+        pend = atomicAdd(ctrs, 1u);
+        s_idx[0] = i0 < n_items ? i0 : n_items;
+        s_idx[1] = i1 < n_items ? i1 : n_items;
+        if (i0 < n_items) copy_record(&s_rec[0], items + i0);
+        if (i1 < n_items) copy_record(&s_rec[1], items + i1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (i0 < n_items) wait_for(0);
     }
     __syncthreads();
-    if (s_it[0] < n_items) stage(0, s_it[0]);
+    if (s_idx[0] < n_items) stage(0, s_rec[0]);
     asm volatile("cp.async.commit_group;" ::: "memory");
 
     for (unsigned k = 0;; ++k) {
-        const int b = k & 1;
-        const unsigned it = s_it[b];
-        if (it >= n_items) break;
-        if (tid == 0) fetch(b ^ 1);
-        __syncthreads();  // s_it[b ^ 1], s_ready
-        const unsigned nx = s_it[b ^ 1];
-        const bool early = nx < n_items && s_ready;
-        if (early) stage(b ^ 1, nx);
+        const int b = k & 1, r = k % 3, r1 = (k + 1) % 3, r2 = (k + 2) % 3;
+        if (s_idx[r] >= n_items) break;
+        if (tid == 0) {
+            asm volatile("cp.async.wait_all;" ::: "memory");  // the record of item k + 1
+            int ready = 1;
+            if (s_idx[r1] < n_items && s_rec[r1].dep) ready = ld_acquire(ctrs + s_rec[r1].dep) >= s_rec[r1].target;
+            s_ready = ready;
+        }
+        __syncthreads();  // s_ready, and the record of item k + 1
+        bool early = s_idx[r1] < n_items && s_ready;
+        if (early) stage(b ^ 1, s_rec[r1]);
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (early) asm volatile("cp.async.wait_group 1;" ::: "memory");
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();  // every thread's copies of the current item (and its arguments) landed
+        if (tid == 0) {   // the record of item k + 2 and the index of item k + 3
+            const unsigned i2 = pend < n_items ? pend : n_items;
+            s_idx[r2] = i2;
+            if (i2 < n_items) copy_record(&s_rec[r2], items + i2);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            pend = atomicAdd(ctrs, 1u);
+        }
 
-        const ItemDev item = items[it];
+        const ItemDev &item = s_rec[r];
         const JobDev *J = jobs + item.job;
         const int kind = J->kind;
         unsigned char *buf = smem_raw + b * buf_bytes;
@@ -408,13 +412,17 @@ __global__ void __launch_bounds__(BT, 3)
         // them visible (cumulatively) to whoever acquires the counters
         if (tid == 0) {
             __threadfence();
-            if ((!BL || kind == JK_NTT) && J->twopass && item.pass == 0) atomicAdd(poly_ctr + J->poly_base + item.poly, 1u);
-            atomicAdd(job_ctr + item.job, 1u);
+            if (item.bump) atomicAdd(ctrs + item.bump, 1u);
+            atomicAdd(ctrs + 2 + item.job, 1u);
         }
-        if (nx < n_items && !early) {  // the next item was not ready: wait for it now, then stage it
-            if (tid == 0) wait_for(b ^ 1);
+        // re-read from shared memory rather than keep registers live across the transform
+        // (s_ready and s_idx[r1] change only at the next item's start or in the late path below)
+        early = s_ready;
+        if (s_idx[(k + 1) % 3] < n_items && !early) {  // the next item was not ready: wait for it now, then stage it
+            const int q1 = (k + 1) % 3;
+            if (tid == 0) wait_for(q1);
             __syncthreads();
-            if (s_it[b ^ 1] < n_items) stage(b ^ 1, s_it[b ^ 1]);
+            if (s_idx[q1] < n_items) stage((k & 1) ^ 1, s_rec[q1]);
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
     }
