@@ -165,6 +165,64 @@ class ClockSampler:
                 "samples_busy": len(busy)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons polled through NVML (read-only queries) every ~0.5 ms from a
+    host thread while the timed steps run; the nvidia-smi sampler above is the fallback."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import ctypes
+        self.ok, self.rows, self.stop_ev, self.t = False, [], threading.Event(), None
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            import torch
+            self.h = ctypes.c_void_p()
+            uuid = str(getattr(torch.cuda.get_device_properties(torch_device), "uuid", ""))
+            found = False
+            if uuid:
+                key = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+                found = self.lib.nvmlDeviceGetHandleByUUID(key.encode(), ctypes.byref(self.h)) == 0
+            if not found:
+                found = self.lib.nvmlDeviceGetHandleByIndex_v2(torch_device.index or 0, ctypes.byref(self.h)) == 0
+            self.ok = found
+            self.c = ctypes
+        except Exception:
+            self.ok = False
+
+    def _poll(self):
+        c = self.c
+        mhz, mx, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_ev.is_set():
+            if (self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(mhz)) == 0 and
+                    self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, c.byref(mx)) == 0 and
+                    get_reasons(self.h, c.byref(rs)) == 0):
+                self.rows.append((mhz.value, mx.value, rs.value))
+            time.sleep(0.0005)
+
+    def start(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+
+    def stop(self):
+        if self.t:
+            self.stop_ev.set()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return None
+        reasons = sorted({n for _, _, r in self.rows for bit, n in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": reasons, "samples": len(self.rows), "source": "NVML, polled every ~0.5 ms during the timed steps"}
+
+
 # ----------------------------------------------------------------------------------- replicas
 
 def aggregate(ms_local: float, units_local: float, world: int, device=None):
@@ -232,7 +290,7 @@ def run_gpu(args, rank, world):
         for b in range(batch):
             M.ntt_inverse(plan, d[b * N:(b + 1) * N], 1, N, stream=sh)
 
-    def timed(step, steps, warmup, sampler_idx=None):
+    def timed(step, steps, warmup, sampler=None):
         """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed between."""
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -241,6 +299,8 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
             if world > 1:
                 torch.distributed.barrier()
+            if sampler:
+                sampler.start()
             times = []
             for _ in range(steps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -250,6 +310,8 @@ def run_gpu(args, rank, world):
                 flush_l2(flush)
                 times.append((e0, e1))
             torch.cuda.synchronize()
+            if sampler:
+                sampler.stop()
             if world > 1:
                 torch.distributed.barrier()
         return [a.elapsed_time(b) for a, b in times]
@@ -271,9 +333,10 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in fw], [a.elapsed_time(b) for a, b in iv]
 
+    nvml = NvmlClocks(dev)
     with ClockSampler(dev.index) as clk:
-        t_batched = timed(step_batched, args.steps, args.warmup)
-        clocks = clk.summary()
+        t_batched = timed(step_batched, args.steps, args.warmup, nvml)
+        clocks = nvml.summary() or clk.summary()
     bfly = 2 * wl["butterflies_per_dir"]
     ms, value = aggregate(sum(t_batched) / len(t_batched), bfly, world, dev)
 
@@ -335,11 +398,13 @@ def run_gpu(args, rank, world):
     hbm_peak = hbm_peak or HBM_FALLBACK_GBS
     hbm_achieved = bytes_per_launch / (ms_launch * 1e-3) / 1e9
     alu_frac, hbm_frac = alu_achieved / alu_peak, hbm_achieved / hbm_peak
+    kname = "persistent_kernel" if args.form == "split" else "prefetch_kernel"
+    traffic = profiled_traffic(f"{kname}_uniform_{batch}x{N}_{args.bits}bit.md")
+    kdesc = f"{kname} (the batched form; one launch = one step)"
     if alu_frac >= hbm_frac:
         out["roofline"] = {"bound": "alu", "achieved": alu_achieved / 1e12, "peak": alu_peak / 1e12,
                            "unit": "T mad32/s", "frac": alu_frac,
-                           "traffic": profiled_traffic(f"persistent_kernel_uniform_{batch}x{N}_{args.bits}bit.md"),
-                           "kernel": "persistent_kernel (one launch = one step)",
+                           "traffic": traffic, "kernel": kdesc,
                            "peak_source": "measured by mq_probe_imad_rate (carry-chained mad.lo.cc/madc.hi.cc)",
                            "algorithmic": f"{mads_per_mul} 32-bit multiply instructions per Shoup product",
                            "hbm_frac": hbm_frac, "hbm_achieved_gbs": hbm_achieved,
@@ -347,8 +412,7 @@ def run_gpu(args, rank, world):
     else:
         out["roofline"] = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                            "frac": hbm_frac,
-                           "traffic": profiled_traffic(f"persistent_kernel_uniform_{batch}x{N}_{args.bits}bit.md"),
-                           "kernel": "persistent_kernel (one launch = one step)",
+                           "traffic": traffic, "kernel": kdesc,
                            "peak_source": hbm_src, "alu_frac": alu_frac, "ms_launch": ms_launch,
                            "alu_achieved_tmads": alu_achieved / 1e12, "alu_peak_tmads": alu_peak / 1e12}
     out["roofline"]["call_form_alu_frac"] = (mad_f + mad_i) / ((ms_f + ms_i) * 1e-3) / alu_peak
