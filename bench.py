@@ -53,6 +53,7 @@ def parse():
                    help="uniform: the default line (uniform batch, plus BLAS and the uneven batch as extra blocks); "
                         "serve: the Poisson serving sweep")
     p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--no-polymul", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=1.5)
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
@@ -440,9 +441,54 @@ def run_gpu(args, rank, world):
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
     if not args.no_uneven:
         out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args))
+    if not args.no_polymul:
+        out["polymul"] = bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul,
+                                       alu_peak, args)
 
     out["clocks"] = clocks
     return out
+
+
+def bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul, alu_peak, args):
+    """The batch's polynomial products c_i = a_i * b_i mod (x^N + 1): ntt_polymul (the product fused
+    into the pass holding the last forward and first inverse stages) against the unfused sequence
+    ntt_forward(a), ntt_forward(b), mod_vmul, ntt_inverse on the same operands (on stream `sh`,
+    the one `timed` records its events on)."""
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(77)
+    b = dev_residues(torch, batch * N, q, width, gen, dev).view_as(d)
+    c = torch.empty_like(d)
+    ta, tb = d.clone(), b.clone()
+    # bit-exactness of what is timed: fused and unfused on the same inputs
+    M.ntt_polymul(plan, c, d, b, batch, N, stream=sh)
+    M.ntt_forward(plan, ta, batch, N, stream=sh)
+    M.ntt_forward(plan, tb, batch, N, stream=sh)
+    M.mod_vmul(ta, ta, tb, batch * N, q, width, stream=sh)
+    M.ntt_inverse(plan, ta, batch, N, stream=sh)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(c, ta))
+
+    def step_fused():
+        M.ntt_polymul(plan, c, d, b, batch, N, stream=sh)
+
+    def step_unfused():   # in place on the copies: the arithmetic's cost does not depend on the values
+        M.ntt_forward(plan, ta, batch, N, stream=sh)
+        M.ntt_forward(plan, tb, batch, N, stream=sh)
+        M.mod_vmul(ta, ta, tb, batch * N, q, width, stream=sh)
+        M.ntt_inverse(plan, ta, batch, N, stream=sh)
+
+    ms_f = statistics.median(timed(step_fused, args.steps, args.warmup))
+    ms_u = statistics.median(timed(step_unfused, args.steps, args.warmup))
+    barrett_mads = 80 if width == 2 else 20   # 32-bit multiply instructions per Barrett product
+    mads = (3 * wl["butterflies_per_dir"] + batch * N // 2) * mads_per_mul + batch * N * barrett_mads
+    del b, c, ta, tb
+    return {"workload": f"{batch} products of degree-{N} polynomials mod (x^N + 1), {q.bit_length()}-bit q",
+            "products_per_s": batch / (ms_f * 1e-3), "ms_fused": ms_f, "ms_unfused": ms_u,
+            "fused_over_unfused": ms_u / ms_f, "bit_exact_vs_unfused": same,
+            "launches_fused": 1 if N <= 4096 else 4, "launches_unfused": (1 if N <= 4096 else 2) * 3 + 1,
+            "alu_frac": mads / (ms_f * 1e-3) / alu_peak,
+            "alu_count": f"3 transforms x {mads_per_mul} per butterfly + N/2 scale products + N Barrett products "
+                         f"x {barrett_mads} (32-bit multiply instructions)"}
 
 
 def bench_blas(M, torch, dev, stream, flush):

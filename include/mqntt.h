@@ -97,6 +97,23 @@ int ntt_forward(const ntt_plan *plan, void *d_data, size_t batch, size_t stride,
 int ntt_inverse(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
 
 /*
+ * Polynomial product through the NTT (Sec. 2.3, polynomial multiplication using NTT): for each of
+ * `batch` polynomials, c = a * b in Z_q[X]/(X^N + 1) -- the negacyclic product, the ring of FHE --
+ * with the plan's N and q (a plan created with MQ_CYCLIC gives the cyclic product, mod X^N - 1).
+ * Computes the inverse transform of the pointwise product of the two forward transforms, with the
+ * pointwise product fused into the pass that holds the last forward and the first inverse stages
+ * (for N <= 2^12 the whole product is one kernel).  The plan's order flag does not matter.
+ * d_c, d_a, d_b: device buffers of `batch` polynomials `stride` residues apart (stride >= N;
+ * ignored if batch = 1), coefficients canonical (< q) in natural order, 8 * width-byte aligned;
+ * the result is canonical, in natural order.  d_c may be d_a or d_b (in place); other overlaps
+ * are undefined.  a and b are not modified unless c is one of them.  For N > 2^12 the call takes
+ * batch * N residues of stream-ordered scratch from the library's pool.  batch == 0 is a no-op.
+ * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
+ */
+int ntt_polymul(const ntt_plan *plan, void *d_c, const void *d_a, const void *d_b, size_t batch, size_t stride,
+                void *stream);
+
+/*
  * ntt_forward without any device allocation (the paper has no counterpart: this is a deployment
  * variant).  For callers that cannot allocate device memory while running -- a service that
  * reserves its memory budget at start-up, code sharing the GPU with a framework whose allocator

@@ -289,6 +289,83 @@ extern "C" int ntt_inverse(const ntt_plan *p, void *d, size_t batch, size_t stri
     return ntt_run(p, d, batch, stride, stream, true);
 }
 
+// c = a * b in Z_q[X]/(X^N + 1) (X^N - 1 for a cyclic plan): forward transforms of a and b in
+// bit-reversed order, pointwise product, inverse transform (Sec. 2.3).  The product is fused into
+// the pass that holds the last forward and the first inverse stages (polymul.cuh); for N > 2^12 the
+// column passes run before (a into c, b into scratch) and after it (inverse, N^-1 folded in).
+extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void *b, size_t batch, size_t stride,
+                           void *stream) {
+    if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
+    if (batch == 0) return MQ_OK;
+    int rc;
+    if ((rc = check_ptr(c, p->width, "d_c")) || (rc = check_ptr(a, p->width, "d_a")) ||
+        (rc = check_ptr(b, p->width, "d_b")))
+        return rc;
+    const size_t N = (size_t)1 << p->log2n;
+    if (batch == 1) stride = N;
+    if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
+    if (batch > (SIZE_MAX / 16) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
+    MulArgs m;
+    memcpy(m.q, p->q, sizeof m.q);
+    memcpy(m.mu, p->mu, sizeof m.mu);
+    m.L = p->L;
+    // the fused pass: forward row stages of a (fa) and b (fb), product, inverse row stages (ia)
+    PassArgs fa = pass_base(p, false, batch), ia = pass_base(p, true, batch);
+    fa.col = ia.col = 0;
+    fa.in_layout = fa.out_layout = ia.in_layout = ia.out_layout = LAYOUT_ROW;
+    ia.out = c;
+    ia.out_stride = stride;
+    if (L1 == 0) {  // one pass: the whole product in one kernel
+        fa.in = a;
+        fa.in_stride = stride;
+        PassArgs fb = fa;
+        fb.in = b;
+        ia.scale = ia.final = 1;
+        cudaError_t e = launch_polymul(p->width, logN, fa, fb, ia, m, s);
+        return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "polynomial product launch");
+    }
+    void *scr = nullptr;
+    rc = mq_pool_alloc(&scr, batch * N * 8u * (size_t)p->width, s);
+    if (rc) return rc;
+    // forward column passes: b into the scratch first, then a into c (so c may alias a or b)
+    PassArgs col = pass_base(p, false, batch);
+    col.col = 1;
+    col.in_layout = col.out_layout = LAYOUT_COL;
+    col.in = b;
+    col.in_stride = stride;
+    col.out = scr;
+    col.out_stride = N;
+    rc = run_pass(p, false, col, L1, s);
+    if (!rc) {
+        col.in = a;
+        col.out = c;
+        col.out_stride = stride;
+        rc = run_pass(p, false, col, L1, s);
+    }
+    if (!rc) {
+        fa.in = c;
+        fa.in_stride = stride;
+        PassArgs fb = fa;
+        fb.in = scr;
+        fb.in_stride = N;
+        cudaError_t e = launch_polymul(p->width, L2, fa, fb, ia, m, s);
+        if (e != cudaSuccess) rc = mq_cuda_fail(e, "polynomial product launch");
+    }
+    if (!rc) {  // inverse column pass with the N^-1 scale, canonical result
+        PassArgs icol = pass_base(p, true, batch);
+        icol.col = 1;
+        icol.in_layout = icol.out_layout = LAYOUT_COL;
+        icol.in = icol.out = c;
+        icol.in_stride = icol.out_stride = stride;
+        icol.scale = icol.final = 1;
+        rc = run_pass(p, true, icol, L1, s);
+    }
+    int rc2 = mq_pool_free(scr, s);
+    return rc ? rc : rc2;
+}
+
 // ------------------------------------------------------------------------------------------------
 // BLAS
 // ------------------------------------------------------------------------------------------------

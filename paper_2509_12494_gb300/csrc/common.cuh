@@ -47,6 +47,18 @@ struct PassArgs {
 // Launch one pass; returns a cudaError_t.  L = log2 of the tile size, inv = direction.
 cudaError_t launch_ntt_pass(int width, int L, bool inv, const PassArgs &a, cudaStream_t s);
 
+// The Barrett constants of a plan's modulus, for the pointwise product of the fused polynomial
+// product (see polymul.cuh).
+struct MulArgs {
+    uint64_t q[2], mu[2];
+    int L;  // bit length of q
+};
+
+// Launch the fused pass of the polynomial product on tiles of 2^L residues: forward rounds of fa
+// (a's tiles) and fb (b's tiles), pointwise product, inverse rounds and store of ia.
+cudaError_t launch_polymul(int width, int L, const PassArgs &fa, const PassArgs &fb, const PassArgs &ia,
+                           const MulArgs &m, cudaStream_t s);
+
 // Build twiddle tables on the device (see ntt.cu).
 cudaError_t launch_twiddle_build(int width, int logN, int cyclic, const uint64_t q[2], const uint64_t root[2],
                                  const uint64_t root_inv[2], const uint64_t mu[2], int L, void *tw_fwd,

@@ -259,6 +259,39 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
     tile_sync<BAR, S::NT>();
 }
 
+// The register rounds of one pass on the CTA's staged tiles: every full round (three stages) runs
+// the same code in a loop; a shorter round, when L is not a multiple of 3, has its own (forward:
+// last, inverse: first).  Called by NT = Shape::NT threads; ends with a barrier.
+template <int W, int L, bool INV, int BAR = 0>
+__device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long long first_tile,
+                                            typename Traits<W>::E *sm, int tid) {
+    typedef Traits<W> Tr;
+    typedef typename Tr::E E;
+    typedef Shape<W, L> S;
+    const E q = Tr::make(a.q);
+    const E q4 = add_nored(add_nored(q, q), add_nored(q, q));
+    const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
+    const int g = tid / S::TPT, t = tid % S::TPT;
+    unsigned tw_base;
+    {
+        const TileAddr ta(a);
+        unsigned long long gt = first_tile + g;
+        unsigned ti = (unsigned)(gt & ta.mask);
+        tw_base = a.col ? 1u : ((1u << a.L1) + (a.perm ? brv(ti, a.L1) : ti));
+    }
+    E *tile = sm + g * S::TS;
+    constexpr int FULL = L / S::r, PART = L - FULL * S::r;
+    if (!INV) {
+#pragma unroll 1
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
+        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
+    } else {
+        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
+#pragma unroll 1
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
+    }
+}
+
 // One CTA's share of a pass on tiles already staged in `sm` (by load_tiles_*): tiles
 // first_tile .. first_tile + G - 1 of the batch, a tile past the last polynomial being skipped.
 // Called by NT = Shape::NT threads with thread index tid after a barrier that follows the staging;
@@ -286,30 +319,10 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
     const TileAddr ta(a);
     const int lgTP = ta.lgTP;
     const unsigned long long tp_mask = ta.mask;
-    const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
     E *out = reinterpret_cast<E *>(a.out);
     const bool gfast_out = a.out_layout != LAYOUT_ROW;
 
-    // ---- register rounds: every full round (three stages) runs the same code in a loop; a
-    // shorter round, when L is not a multiple of 3, has its own (forward: last, inverse: first)
-    const int g = tid / S::TPT, t = tid % S::TPT;
-    unsigned tw_base;
-    {
-        unsigned long long gt = first_tile + g;
-        unsigned ti = (unsigned)(gt & tp_mask);
-        tw_base = a.col ? 1u : ((1u << L1) + (a.perm ? brv(ti, L1) : ti));
-    }
-    E *tile = sm + g * S::TS;
-    constexpr int FULL = L / S::r, PART = L - FULL * S::r;
-    if (!INV) {
-#pragma unroll 1
-        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
-        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
-    } else {
-        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
-#pragma unroll 1
-        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
-    }
+    tile_rounds<W, L, INV, BAR>(a, first_tile, sm, tid);
 
     // ---- shared -> global (canonical residues from the last pass)
     for (int i = tid; i < S::G * S::T; i += S::NT) {

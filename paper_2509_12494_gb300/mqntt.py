@@ -56,6 +56,7 @@ def load(build_if_missing: bool = False):
         "ntt_plan_destroy": [_vp],
         "ntt_forward": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_inverse": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
+        "ntt_polymul": [_vp, _vp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_forward_noalloc": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_plan_info": [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint)],
         "mod_vadd": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
@@ -161,6 +162,11 @@ def ntt_forward(plan: Plan, data, batch: int = 1, stride: int = 0, stream=None):
 
 def ntt_inverse(plan: Plan, data, batch: int = 1, stride: int = 0, stream=None):
     _check(load().ntt_inverse(plan.handle, ptr(data), batch, stride, stream_handle(stream)))
+
+
+def ntt_polymul(plan: Plan, c, a, b, batch: int = 1, stride: int = 0, stream=None):
+    """c = a * b mod (X^N + 1, q) (mod X^N - 1 for a cyclic plan), per polynomial."""
+    _check(load().ntt_polymul(plan.handle, ptr(c), ptr(a), ptr(b), batch, stride, stream_handle(stream)))
 
 
 MQ_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -91,3 +91,9 @@ def test_axpy_scalar_range(lib):
     with pytest.raises(M.MqError) as e:
         M.mod_axpy(16, Q124, 16, 4, Q124, M.MQ_W128, stream=0)
     assert e.value.code == M.MQ_ERR_RANGE
+
+
+def test_polymul_rejects_without_touching_the_device(lib):
+    so = M.load()
+    assert so.ntt_polymul(None, 16, 16, 16, 1, 0, None) == M.MQ_ERR_ARG
+    assert "plan" in M.mq_last_error()
