@@ -142,77 +142,107 @@ __device__ __forceinline__ void mul_wide32(uint32_t a, uint32_t b, uint32_t &lo,
     hi = (uint32_t)(p >> 32);
 }
 
-// Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  The 16 limb products
-// are accumulated in two carry chains: E takes the products of the even limbs a0, a2 and O those
-// of the odd limbs a1, a3, so that within one row (one limb b_i) the lo and hi halves of a chain
-// land in consecutive columns.  Row 0 needs no additions; every later row ends in a fresh limb
-// (hi half plus the incoming carry, which cannot overflow), so no separate carry propagation is
-// needed.  A final 7-limb addition merges the two chains: 32 multiply instructions and 7 adds.
+// Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  Each 32 x 32 -> 64 limb
+// product a_j b_i is added into a pair of consecutive columns (i + j, i + j + 1) by a mad.lo.cc /
+// madc.hi.cc pair, which the GPU executes as one wide multiply-add on an aligned register pair.
+// To keep every pair aligned the products are split by the parity of i + j: E holds the pairs
+// (0,1), (2,3), (4,5), (6,7) and takes the products with i + j even, O holds (1,2), (3,4), (5,6),
+// (7,8) and takes those with i + j odd, so a chain never has to move its columns by one.  Within
+// a chain a row of two products either ends in a column not written before (its high half plus
+// the incoming carry cannot overflow) or hands its carry to the next, still empty, column.  A final
+// 7-limb addition merges E and O: 32 multiply instructions and 9 adds.
 __device__ __forceinline__ void mul_wide(const uint4 a, const uint4 b, uint32_t c[8]) {
-    uint32_t E0, E1, E2, E3, E4, E5, E6, O1, O2, O3, O4, O5, O6, O7;
-    mul_wide32(a.x, b.x, E0, E1);  // row 0: four disjoint 64-bit products, no additions
+    uint32_t E0, E1, E2, E3, E4, E5, E6, E7, O1, O2, O3, O4, O5, O6, O7;
+    // b0: a0 b0 -> E(0,1), a2 b0 -> E(2,3), a1 b0 -> O(1,2), a3 b0 -> O(3,4); no additions
+    mul_wide32(a.x, b.x, E0, E1);
     mul_wide32(a.z, b.x, E2, E3);
     mul_wide32(a.y, b.x, O1, O2);
     mul_wide32(a.w, b.x, O3, O4);
-#define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
-    asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
-        "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \
-        "madc.lo.cc.u32 %2, %10, %12, %2;\n\t"                                                \
-        "madc.hi.u32    %3, %10, %12, 0;\n\t"                                                 \
-        "mad.lo.cc.u32  %4, %9, %12, %4;\n\t"                                                 \
-        "madc.hi.cc.u32 %5, %9, %12, %5;\n\t"                                                 \
-        "madc.lo.cc.u32 %6, %11, %12, %6;\n\t"                                                \
-        "madc.hi.u32    %7, %11, %12, 0;"                                                       \
-        : "+r"(e0), "+r"(e1), "+r"(e2), "=r"(e3), "+r"(o1), "+r"(o2), "+r"(o3), "=r"(o4)       \
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(bi));
-    MQ_ROW(E1, E2, E3, E4, O2, O3, O4, O5, b.y)
-    MQ_ROW(E2, E3, E4, E5, O3, O4, O5, O6, b.z)
-    MQ_ROW(E3, E4, E5, E6, O4, O5, O6, O7, b.w)
-#undef MQ_ROW
+    // b1: a1 b1 -> E(2,3), a3 b1 -> E(4,5) (new); a0 b1 -> O(1,2), a2 b1 -> O(3,4), carry -> O5
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, 0;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(E2), "+r"(E3), "=r"(E4), "=r"(E5)
+        : "r"(a.y), "r"(a.w), "r"(b.y));
+    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
+        "addc.u32       %4, 0, 0;"
+        : "+r"(O1), "+r"(O2), "+r"(O3), "+r"(O4), "=r"(O5)
+        : "r"(a.x), "r"(a.z), "r"(b.y));
+    // b2: a0 b2 -> E(2,3), a2 b2 -> E(4,5), carry -> E6; a1 b2 -> O(3,4), a3 b2 -> O(5,6) (O6 new)
+    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
+        "addc.u32       %4, 0, 0;"
+        : "+r"(E2), "+r"(E3), "+r"(E4), "+r"(E5), "=r"(E6)
+        : "r"(a.x), "r"(a.z), "r"(b.z));
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(O3), "+r"(O4), "+r"(O5), "=r"(O6)
+        : "r"(a.y), "r"(a.w), "r"(b.z));
+    // b3: a1 b3 -> E(4,5), a3 b3 -> E(6,7) (E7 new); a0 b3 -> O(3,4), a2 b3 -> O(5,6), carry -> O7
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(E4), "+r"(E5), "+r"(E6), "=r"(E7)
+        : "r"(a.y), "r"(a.w), "r"(b.w));
+    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
+        "addc.u32       %4, 0, 0;"
+        : "+r"(O3), "+r"(O4), "+r"(O5), "+r"(O6), "=r"(O7)
+        : "r"(a.x), "r"(a.z), "r"(b.w));
     c[0] = E0;
-    asm("add.cc.u32  %0, %7, %13;\n\t"
-        "addc.cc.u32 %1, %8, %14;\n\t"
-        "addc.cc.u32 %2, %9, %15;\n\t"
-        "addc.cc.u32 %3, %10, %16;\n\t"
-        "addc.cc.u32 %4, %11, %17;\n\t"
-        "addc.cc.u32 %5, %12, %18;\n\t"
-        "addc.u32    %6, %19, 0;"
+    asm("add.cc.u32  %0, %7, %14;\n\t"
+        "addc.cc.u32 %1, %8, %15;\n\t"
+        "addc.cc.u32 %2, %9, %16;\n\t"
+        "addc.cc.u32 %3, %10, %17;\n\t"
+        "addc.cc.u32 %4, %11, %18;\n\t"
+        "addc.cc.u32 %5, %12, %19;\n\t"
+        "addc.u32    %6, %13, %20;"
         : "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
-        : "r"(E1), "r"(E2), "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(O1), "r"(O2), "r"(O3), "r"(O4), "r"(O5),
-          "r"(O6), "r"(O7));
+        : "r"(E1), "r"(E2), "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(E7), "r"(O1), "r"(O2), "r"(O3), "r"(O4),
+          "r"(O5), "r"(O6), "r"(O7));
 }
 
-// Low 128 bits of a * b: only the products that reach columns 0..3.
+// Low 128 bits of a * b: only the products that reach columns 0..3, in the parity-split chains
+// of mul_wide (E: pairs (0,1), (2,3); O: the pair (1,2) and column 3, which takes only low halves).
 __device__ __forceinline__ uint4 mul_lo(const uint4 a, const uint4 b) {
-    uint32_t e0, e1, e2, e3, o1, o2, o3;
-    // row 0: a0 b0 -> 0, 1; a2 b0 -> 2, 3; a1 b0 -> 1, 2; lo(a3 b0) -> 3
-    mul_wide32(a.x, b.x, e0, e1);
-    mul_wide32(a.z, b.x, e2, e3);
-    mul_wide32(a.y, b.x, o1, o2);
-    o3 = a.w * b.x;
-    asm("mad.lo.cc.u32  %0, %3, %5, %0;\n\t"
-        "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
-        "madc.lo.u32    %2, %4, %5, %2;"
-        : "+r"(e1), "+r"(e2), "+r"(e3)
-        : "r"(a.x), "r"(a.z), "r"(b.y));
-    asm("mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
-        "madc.hi.u32    %1, %2, %3, %1;"
-        : "+r"(e2), "+r"(e3)
-        : "r"(a.x), "r"(b.z));
-    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(e3) : "r"(a.x), "r"(b.w));
-    // odd limbs (a1, a3), one column up
-    asm("mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
-        "madc.hi.u32    %1, %2, %3, %1;"
-        : "+r"(o2), "+r"(o3)
-        : "r"(a.y), "r"(b.y));
-    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(o3) : "r"(a.y), "r"(b.z));
+    uint32_t E0, E1, E2, E3, O1, O2, O3;
+    mul_wide32(a.x, b.x, E0, E1);  // a0 b0
+    mul_wide32(a.z, b.x, E2, E3);  // a2 b0
+    mul_wide32(a.y, b.x, O1, O2);  // a1 b0
+    O3 = a.w * b.x;                // lo(a3 b0)
+    // even: a1 b1 and a0 b2 -> E(2,3) (carries past column 3 are dropped)
+    asm("mad.lo.cc.u32  %0, %2, %4, %0;\n\t"
+        "madc.hi.u32    %1, %2, %4, %1;\n\t"
+        "mad.lo.cc.u32  %0, %3, %5, %0;\n\t"
+        "madc.hi.u32    %1, %3, %5, %1;"
+        : "+r"(E2), "+r"(E3)
+        : "r"(a.y), "r"(a.x), "r"(b.y), "r"(b.z));
+    // odd: a0 b1 -> O(1,2) with its carry into column 3; lo(a2 b1), lo(a1 b2), lo(a0 b3) -> O3
+    asm("mad.lo.cc.u32  %0, %3, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %6, %1;\n\t"
+        "madc.lo.u32    %2, %4, %6, %2;\n\t"
+        "mad.lo.u32     %2, %5, %7, %2;\n\t"
+        "mad.lo.u32     %2, %3, %8, %2;"
+        : "+r"(O1), "+r"(O2), "+r"(O3)
+        : "r"(a.x), "r"(a.z), "r"(a.y), "r"(b.y), "r"(b.z), "r"(b.w));
     uint4 r;
+    r.x = E0;
     asm("add.cc.u32  %0, %3, %6;\n\t"
         "addc.cc.u32 %1, %4, %7;\n\t"
         "addc.u32    %2, %5, %8;"
         : "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "r"(e1), "r"(e2), "r"(e3), "r"(o1), "r"(o2), "r"(o3));
-    r.x = e0;
+        : "r"(E1), "r"(E2), "r"(E3), "r"(O1), "r"(O2), "r"(O3));
     return r;
 }
 
@@ -228,48 +258,62 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
 
 // floor((a * b - D) / 2^128) where D = a0 b0 + 2^32 (a0 b1 + a1 b0) < 2^98: the high half of the
 // product without the three limb products that only reach columns 0..2.  Since D < 2^128 the
-// result is the true high half or one less.  26 multiply instructions instead of 32 (13 of them
-// high halves instead of 16), in the even/odd chains of mul_wide.
+// result is the true high half or one less.  13 limb products instead of 16, in the parity-split
+// chains of mul_wide (the O pair (1,2) is then empty and column 2 holds only E2, which carries
+// nothing upward by itself, so the merge starts at column 3).
 __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
-    uint32_t E2, E3, E4, E5, E6, O2, O3, O4, O5, O6, O7, h11;
-    // row 0 (b0): only a2 b0 -> columns 2, 3 and a3 b0 -> columns 3, 4
-    mul_wide32(a.z, b.x, E2, E3);
-    mul_wide32(a.w, b.x, O3, O4);
-    // row 1 (b1): a2 b1 -> 3, 4 (even chain); a1 b1 -> 2, 3 and a3 b1 -> 4, 5 (odd chain)
-    mul_wide32(a.y, b.y, O2, h11);
+    uint32_t E2, E3, E4, E5, E6, E7, O3, O4, O5, O6, O7;
+    mul_wide32(a.z, b.x, E2, E3);  // a2 b0
+    mul_wide32(a.w, b.x, O3, O4);  // a3 b0
+    // b1: a1 b1 -> E(2,3), a3 b1 -> E(4,5) (new); a2 b1 -> O(3,4), carry -> O5
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, 0;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(E2), "+r"(E3), "=r"(E4), "=r"(E5)
+        : "r"(a.y), "r"(a.w), "r"(b.y));
+    asm("mad.lo.cc.u32  %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32       %2, 0, 0;"
+        : "+r"(O3), "+r"(O4), "=r"(O5)
+        : "r"(a.z), "r"(b.y));
+    // b2: a0 b2 -> E(2,3), a2 b2 -> E(4,5), carry -> E6; a1 b2 -> O(3,4), a3 b2 -> O(5,6) (O6 new)
     asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
-        "madc.hi.u32    %1, %5, %7, 0;\n\t"
-        "add.cc.u32     %2, %2, %6;\n\t"
-        "madc.lo.cc.u32 %3, %8, %7, %3;\n\t"
-        "madc.hi.u32    %4, %8, %7, 0;"
-        : "+r"(E3), "=r"(E4), "+r"(O3), "+r"(O4), "=r"(O5)
-        : "r"(a.z), "r"(h11), "r"(b.y), "r"(a.w));
-#define MQ_ROW(e0, e1, e2, e3, o1, o2, o3, o4, bi)                                            \
-    asm("mad.lo.cc.u32  %0, %8, %12, %0;\n\t"                                                 \
-        "madc.hi.cc.u32 %1, %8, %12, %1;\n\t"                                                 \
-        "madc.lo.cc.u32 %2, %10, %12, %2;\n\t"                                                \
-        "madc.hi.u32    %3, %10, %12, 0;\n\t"                                                 \
-        "mad.lo.cc.u32  %4, %9, %12, %4;\n\t"                                                 \
-        "madc.hi.cc.u32 %5, %9, %12, %5;\n\t"                                                 \
-        "madc.lo.cc.u32 %6, %11, %12, %6;\n\t"                                                \
-        "madc.hi.u32    %7, %11, %12, 0;"                                                       \
-        : "+r"(e0), "+r"(e1), "+r"(e2), "=r"(e3), "+r"(o1), "+r"(o2), "+r"(o3), "=r"(o4)       \
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(bi));
-    MQ_ROW(E2, E3, E4, E5, O3, O4, O5, O6, b.z)
-    MQ_ROW(E3, E4, E5, E6, O4, O5, O6, O7, b.w)
-#undef MQ_ROW
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
+        "addc.u32       %4, 0, 0;"
+        : "+r"(E2), "+r"(E3), "+r"(E4), "+r"(E5), "=r"(E6)
+        : "r"(a.x), "r"(a.z), "r"(b.z));
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(O3), "+r"(O4), "+r"(O5), "=r"(O6)
+        : "r"(a.y), "r"(a.w), "r"(b.z));
+    // b3: a1 b3 -> E(4,5), a3 b3 -> E(6,7) (E7 new); a0 b3 -> O(3,4), a2 b3 -> O(5,6), carry -> O7
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32    %3, %5, %6, 0;"
+        : "+r"(E4), "+r"(E5), "+r"(E6), "=r"(E7)
+        : "r"(a.y), "r"(a.w), "r"(b.w));
+    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
+        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
+        "addc.u32       %4, 0, 0;"
+        : "+r"(O3), "+r"(O4), "+r"(O5), "+r"(O6), "=r"(O7)
+        : "r"(a.x), "r"(a.z), "r"(b.w));
     uint4 r;
-    uint32_t c2, c3;
-    asm("add.cc.u32  %0, %6, %12;\n\t"
-        "addc.cc.u32 %1, %7, %13;\n\t"
-        "addc.cc.u32 %2, %8, %14;\n\t"
-        "addc.cc.u32 %3, %9, %15;\n\t"
-        "addc.cc.u32 %4, %10, %16;\n\t"
-        "addc.u32    %5, %11, %17;"
-        : "=r"(c2), "=r"(c3), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "r"(E2), "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(0u), "r"(O2), "r"(O3), "r"(O4), "r"(O5), "r"(O6),
-          "r"(O7));
-    (void)c2;
+    uint32_t c3;
+    asm("add.cc.u32  %0, %5, %10;\n\t"
+        "addc.cc.u32 %1, %6, %11;\n\t"
+        "addc.cc.u32 %2, %7, %12;\n\t"
+        "addc.cc.u32 %3, %8, %13;\n\t"
+        "addc.u32    %4, %9, %14;"
+        : "=r"(c3), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(E7), "r"(O3), "r"(O4), "r"(O5), "r"(O6), "r"(O7));
     (void)c3;
     return r;
 }
