@@ -200,7 +200,7 @@ __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned lon
 template <int W, int L, int RR, bool INV, int BAR = 0>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
                                             int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
-                                            typename Traits<W>::E q4) {
+                                            typename Traits<W>::E q4, typename Traits<W>::E nq) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
     typedef Shape<W, L> S;
@@ -234,19 +234,19 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                 if (!INV) {
                     Tr::load_tw(tw, idx, w, wp);
                     E uu = csub(u, q4);                              // [0, 4q)
-                    E tv = mul_mod_shoup_lazy(v, w, wp, q);          // [0, 3q)
+                    E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 3q)
                     u = add_nored(uu, tv);                           // [0, 7q)
                     v = add_sub(uu, q4, tv);                         // (q, 8q)
                 } else if (s == 0 && a.scale) {
                     E dif = add_sub(u, q4, v);                       // (0, 8q)
                     E sum = add_nored(u, v);                         // [0, 8q)
-                    u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q);
-                    v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q);
+                    u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q, nq);
+                    v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q, nq);
                 } else {
                     Tr::load_tw(tw, idx, w, wp);
                     E dif = add_sub(u, q4, v);                       // (0, 8q)
                     u = csub(add_nored(u, v), q4);                   // [0, 4q)
-                    v = mul_mod_shoup_lazy(dif, w, wp, q);           // [0, 3q)
+                    v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 3q)
                 }
             }
         }
@@ -270,6 +270,7 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
     typedef Shape<W, L> S;
     const E q = Tr::make(a.q);
     const E q4 = add_nored(add_nored(q, q), add_nored(q, q));
+    const E nq = neg(q);
     const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
     const int g = tid / S::TPT, t = tid % S::TPT;
     unsigned tw_base;
@@ -283,12 +284,12 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
     constexpr int FULL = L / S::r, PART = L - FULL * S::r;
     if (!INV) {
 #pragma unroll 1
-        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
-        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4, nq);
+        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4, nq);
     } else {
-        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4);
+        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4, nq);
 #pragma unroll 1
-        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4);
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4, nq);
     }
 }
 

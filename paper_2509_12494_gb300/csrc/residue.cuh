@@ -52,10 +52,13 @@ __device__ __forceinline__ uint64_t mul_mod_shoup(uint64_t a, uint64_t w, uint64
     return (r >= q) ? r - q : r;
 }
 
-// a * w mod q up to one multiple of q: in [0, 2q) (the final Shoup correction skipped).
-__device__ __forceinline__ uint64_t mul_mod_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t q) {
+// a * w mod q up to one multiple of q: in [0, 2q) (the final Shoup correction skipped).  nq = -q
+// mod 2^64 (unused here: the 64-bit remainder is one multiply-subtract either way).
+__device__ __forceinline__ uint64_t mul_mod_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t q, uint64_t nq) {
+    (void)nq;
     return a * w - __umul64hi(a, wp) * q;
 }
+__device__ __forceinline__ uint64_t neg(uint64_t q) { return 0 - q; }
 __device__ __forceinline__ uint64_t csub(uint64_t a, uint64_t m) { return a >= m ? a - m : a; }
 __device__ __forceinline__ uint64_t add_nored(uint64_t a, uint64_t b) { return a + b; }
 __device__ __forceinline__ uint64_t add_sub(uint64_t a, uint64_t b2, uint64_t c) { return a + b2 - c; }
@@ -104,6 +107,18 @@ __device__ __forceinline__ uint4 sub128(uint4 a, uint4 b, uint32_t &mask) {
         "subc.cc.u32 %3, %8, %12;\n\t"
         "subc.u32    %4, 0, 0;"
         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w), "=r"(mask)
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w));
+    return r;
+}
+
+// r = a - b mod 2^128, where the caller needs no borrow.
+__device__ __forceinline__ uint4 sub128(uint4 a, uint4 b) {
+    uint4 r;
+    asm("sub.cc.u32  %0, %4, %8;\n\t"
+        "subc.cc.u32 %1, %5, %9;\n\t"
+        "subc.cc.u32 %2, %6, %10;\n\t"
+        "subc.u32    %3, %7, %11;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w));
     return r;
 }
@@ -246,13 +261,68 @@ __device__ __forceinline__ uint4 mul_lo(const uint4 a, const uint4 b) {
     return r;
 }
 
+// Low 128 bits of a * b + c * d, all twenty limb products in one pair of parity-split chains (the
+// Shoup remainder a w - qhat q is a w + qhat (2^128 - q) mod 2^128, so one chain and one merge
+// replace two low products and a subtraction).
+__device__ __forceinline__ uint4 mul_lo2(const uint4 a, const uint4 b, const uint4 c, const uint4 d) {
+    uint32_t E0, E1, E2, E3, O1, O2, O3;
+    mul_wide32(c.x, d.x, E0, E1);  // c0 d0
+    mul_wide32(c.z, d.x, E2, E3);  // c2 d0
+    mul_wide32(c.y, d.x, O1, O2);  // c1 d0
+    O3 = c.w * d.x;                // lo(c3 d0)
+    // even: a0 b0 -> E(0,1) and a2 b0 -> E(2,3) in one chain; a1 b1, a0 b2, c1 d1, c0 d2 -> E(2,3)
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
+        "madc.hi.u32    %3, %5, %6, %3;"
+        : "+r"(E0), "+r"(E1), "+r"(E2), "+r"(E3)
+        : "r"(a.x), "r"(a.z), "r"(b.x));
+    asm("mad.lo.cc.u32  %0, %2, %6, %0;\n\t"
+        "madc.hi.u32    %1, %2, %6, %1;\n\t"
+        "mad.lo.cc.u32  %0, %3, %7, %0;\n\t"
+        "madc.hi.u32    %1, %3, %7, %1;\n\t"
+        "mad.lo.cc.u32  %0, %4, %8, %0;\n\t"
+        "madc.hi.u32    %1, %4, %8, %1;\n\t"
+        "mad.lo.cc.u32  %0, %5, %9, %0;\n\t"
+        "madc.hi.u32    %1, %5, %9, %1;"
+        : "+r"(E2), "+r"(E3)
+        : "r"(a.y), "r"(a.x), "r"(c.y), "r"(c.x), "r"(b.y), "r"(b.z), "r"(d.y), "r"(d.z));
+    // odd: a1 b0, a0 b1, c0 d1 -> O(1,2), each carrying into column 3 with a low half there;
+    // the other low halves of column 3: a1 b2, a0 b3, c1 d2, c0 d3
+    asm("mad.lo.cc.u32  %0, %3, %10, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %10, %1;\n\t"
+        "madc.lo.u32    %2, %4, %10, %2;\n\t"
+        "mad.lo.cc.u32  %0, %5, %11, %0;\n\t"
+        "madc.hi.cc.u32 %1, %5, %11, %1;\n\t"
+        "madc.lo.u32    %2, %6, %11, %2;\n\t"
+        "mad.lo.cc.u32  %0, %7, %14, %0;\n\t"
+        "madc.hi.cc.u32 %1, %7, %14, %1;\n\t"
+        "madc.lo.u32    %2, %8, %14, %2;\n\t"
+        "mad.lo.u32     %2, %3, %12, %2;\n\t"
+        "mad.lo.u32     %2, %5, %13, %2;\n\t"
+        "mad.lo.u32     %2, %9, %15, %2;\n\t"
+        "mad.lo.u32     %2, %7, %16, %2;"
+        : "+r"(O1), "+r"(O2), "+r"(O3)
+        : "r"(a.y), "r"(a.w), "r"(a.x), "r"(a.z), "r"(c.x), "r"(c.z), "r"(c.y), "r"(b.x), "r"(b.y), "r"(b.z),
+          "r"(b.w), "r"(d.y), "r"(d.z), "r"(d.w));
+    uint4 r;
+    r.x = E0;
+    asm("add.cc.u32  %0, %3, %6;\n\t"
+        "addc.cc.u32 %1, %4, %7;\n\t"
+        "addc.u32    %2, %5, %8;"
+        : "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "r"(E1), "r"(E2), "r"(E3), "r"(O1), "r"(O2), "r"(O3));
+    return r;
+}
+
+__device__ __forceinline__ uint4 neg(uint4 q) { return sub128(make_uint4(0u, 0u, 0u, 0u), q); }
+
 // a * w mod q with w' = floor(w * 2^128 / q); a < 2^128, w < q < 2^124.
 __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4 q) {
     uint32_t h[8];
     mul_wide(a, wp, h);
     uint4 qhat = make_uint4(h[4], h[5], h[6], h[7]);
-    uint32_t m;
-    uint4 r = sub128(mul_lo(a, w), mul_lo(qhat, q), m);  // true remainder or + q; exact mod 2^128
+    uint4 r = mul_lo2(a, w, qhat, neg(q));  // a w - qhat q: true remainder or + q
     return reduce_once(r, q);
 }
 
@@ -320,11 +390,11 @@ __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
 
 // a * w mod q up to two multiples of q: the result is in [0, 3q).  Shoup's quotient estimate is the
 // true quotient or one less, and the truncated high half takes at most one more away.  a may be any
-// value below 2^128 (lazy butterflies feed it values below 8q).
-__device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q) {
+// value below 2^128 (lazy butterflies feed it values below 8q).  nq = 2^128 - q.
+__device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q, uint4 nq) {
+    (void)q;
     uint4 qhat = mul_hi_trunc(a, wp);
-    uint32_t m;
-    return sub128(mul_lo(a, w), mul_lo(qhat, q), m);  // exact: a w - qhat q < 3q < 2^126
+    return mul_lo2(a, w, qhat, nq);  // a w - qhat q mod 2^128, exact since it is < 3q < 2^126
 }
 
 // a >= m ? a - m : a
@@ -334,8 +404,7 @@ __device__ __forceinline__ uint4 add_nored(uint4 a, uint4 b) { return add128(a, 
 
 // a + b2 - c for values that keep the result in [0, 2^128): b2 = 2q, c < 2q
 __device__ __forceinline__ uint4 add_sub(uint4 a, uint4 b2, uint4 c) {
-    uint32_t m;
-    return sub128(add128(a, b2), c, m);
+    return sub128(add128(a, b2), c);
 }
 
 // floor(c / 2^s) for an 8-limb c whose quotient fits in 128 bits; s uniform across the warp.
@@ -365,8 +434,7 @@ __device__ __forceinline__ uint4 mul_mod_barrett(uint4 a, uint4 b, const Mod128 
     uint4 q1 = shr256(x, m.L - 1);     // < 2^(L+1)
     mul_wide(q1, m.mu, t);             // < 2^(2L+2)
     uint4 q3 = shr256(t, m.L + 1);     // true quotient minus 0, 1 or 2
-    uint32_t bm;
-    uint4 r = sub128(make_uint4(x[0], x[1], x[2], x[3]), mul_lo(q3, m.q), bm);  // < 3q < 2^126
+    uint4 r = sub128(make_uint4(x[0], x[1], x[2], x[3]), mul_lo(q3, m.q));  // < 3q < 2^126
     r = reduce_once(r, m.q);
     return reduce_once(r, m.q);
 }
