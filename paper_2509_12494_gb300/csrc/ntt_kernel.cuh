@@ -234,9 +234,9 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                 if (!INV) {
                     Tr::load_tw(tw, idx, w, wp);
                     E uu = csub(u, q4);                              // [0, 4q)
-                    E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 3q)
-                    u = add_nored(uu, tv);                           // [0, 7q)
-                    v = add_sub(uu, q4, tv);                         // (q, 8q)
+                    E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 4q)
+                    u = add_nored(uu, tv);                           // [0, 8q)
+                    v = add_sub(uu, q4, tv);                         // (0, 8q)
                 } else if (s == 0 && a.scale) {
                     E dif = add_sub(u, q4, v);                       // (0, 8q)
                     E sum = add_nored(u, v);                         // [0, 8q)
@@ -246,7 +246,7 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                     Tr::load_tw(tw, idx, w, wp);
                     E dif = add_sub(u, q4, v);                       // (0, 8q)
                     u = csub(add_nored(u, v), q4);                   // [0, 4q)
-                    v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 3q)
+                    v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 4q)
                 }
             }
         }
@@ -299,11 +299,11 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
 // ends with a barrier, after which `sm` may be refilled.
 //
 // Butterflies are lazy (after Harvey): between stages the values stay below 8q (forward) or 4q
-// (inverse), and twiddle products are left in [0, 3q) (128-bit: Shoup with a truncated quotient;
-// 64-bit: Shoup without its final correction, [0, 2q)); the pass flagged `final` canonicalises
-// what it stores.  q < 2^124 (2^60) keeps 8q below the word size.
-//   forward (CT):  u <- u mod 4q;  t = w v mod q + {0, q, 2q};  (u, v) <- (u + t, u + 4q - t)
-//   inverse (GS):  (u, v) <- ((u + v) mod 4q, (u + 4q - v) w mod q + {0, q, 2q})
+// (inverse), and twiddle products are left below 4q (Shoup without its final correction: [0, 4q)
+// at 128 bits, whose quotient comes from a truncated high product, [0, 2q) at 64 bits); the pass
+// flagged `final` canonicalises what it stores.  q < 2^124 (2^60) keeps 8q below the word size.
+//   forward (CT):  u <- u mod 4q;  t = w v mod q + {0, .., 3q};  (u, v) <- (u + t, u + 4q - t)
+//   inverse (GS):  (u, v) <- ((u + v) mod 4q, (u + 4q - v) w mod q + {0, .., 3q})
 // Global loads and stores go through L2 only (.cg), so a pass may read what another SM wrote
 // earlier in the same kernel once the writer's completion is observed.
 template <int W, int L, bool INV, int BAR = 0>

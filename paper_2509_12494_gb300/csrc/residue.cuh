@@ -53,7 +53,8 @@ __device__ __forceinline__ uint64_t mul_mod_shoup(uint64_t a, uint64_t w, uint64
 }
 
 // a * w mod q up to one multiple of q: in [0, 2q) (the final Shoup correction skipped).  nq = -q
-// mod 2^64 (unused here: the 64-bit remainder is one multiply-subtract either way).
+// mod 2^64 is not needed here: the compiler's 64-bit high product and one multiply-subtract measured
+// faster than a truncated high product with the remainder as a w + qhat nq.
 __device__ __forceinline__ uint64_t mul_mod_shoup_lazy(uint64_t a, uint64_t w, uint64_t wp, uint64_t q, uint64_t nq) {
     (void)nq;
     return a * w - __umul64hi(a, wp) * q;
@@ -326,22 +327,17 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
     return reduce_once(r, q);
 }
 
-// floor((a * b - D) / 2^128) where D = a0 b0 + 2^32 (a0 b1 + a1 b0) < 2^98: the high half of the
-// product without the three limb products that only reach columns 0..2.  Since D < 2^128 the
-// result is the true high half or one less.  13 limb products instead of 16, in the parity-split
-// chains of mul_wide (the O pair (1,2) is then empty and column 2 holds only E2, which carries
-// nothing upward by itself, so the merge starts at column 3).
+// floor((a * b - D) / 2^128) where D = a0 b0 + 2^32 (a0 b1 + a1 b0) + 2^64 a2 b0 < 2^128 + 2^98:
+// the high half of the product without the four limb products a0 b0, a1 b0, a0 b1, a2 b0, which
+// reach columns 0..3 only.  Since D < 2 * 2^128 the result is the true high half minus 0, 1 or 2.
+// 12 limb products instead of 16, in the parity-split chains of mul_wide (the O pair (1,2) is
+// empty, and column 2 holds only E2, which carries nothing upward by itself).
 __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
     uint32_t E2, E3, E4, E5, E6, E7, O3, O4, O5, O6, O7;
-    mul_wide32(a.z, b.x, E2, E3);  // a2 b0
     mul_wide32(a.w, b.x, O3, O4);  // a3 b0
-    // b1: a1 b1 -> E(2,3), a3 b1 -> E(4,5) (new); a2 b1 -> O(3,4), carry -> O5
-    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
-        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
-        "madc.lo.cc.u32 %2, %5, %6, 0;\n\t"
-        "madc.hi.u32    %3, %5, %6, 0;"
-        : "+r"(E2), "+r"(E3), "=r"(E4), "=r"(E5)
-        : "r"(a.y), "r"(a.w), "r"(b.y));
+    mul_wide32(a.y, b.y, E2, E3);  // a1 b1
+    mul_wide32(a.w, b.y, E4, E5);  // a3 b1
+    // b1: a2 b1 -> O(3,4), carry -> O5
     asm("mad.lo.cc.u32  %0, %3, %4, %0;\n\t"
         "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
         "addc.u32       %2, 0, 0;"
@@ -388,13 +384,13 @@ __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
     return r;
 }
 
-// a * w mod q up to two multiples of q: the result is in [0, 3q).  Shoup's quotient estimate is the
-// true quotient or one less, and the truncated high half takes at most one more away.  a may be any
-// value below 2^128 (lazy butterflies feed it values below 8q).  nq = 2^128 - q.
+// a * w mod q up to three multiples of q: the result is in [0, 4q).  Shoup's quotient estimate is
+// the true quotient or one less, and the truncated high half takes at most two more away.  a may be
+// any value below 2^128 (lazy butterflies feed it values below 8q).  nq = 2^128 - q.
 __device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q, uint4 nq) {
     (void)q;
     uint4 qhat = mul_hi_trunc(a, wp);
-    return mul_lo2(a, w, qhat, nq);  // a w - qhat q mod 2^128, exact since it is < 3q < 2^126
+    return mul_lo2(a, w, qhat, nq);  // a w - qhat q mod 2^128, exact since it is < 4q < 2^126
 }
 
 // a >= m ? a - m : a
