@@ -6,7 +6,7 @@
  * over 64-bit and 128-bit residues:
  *   - modular BLAS (Sec. 2.3, point-wise polynomial operations): vector add, vector subtract,
  *     point-wise vector multiply and axpy y = a x + y, all mod q;
- *   - the number theoretic transform (Sec. 2.3, Eq. 4) and its inverse, negacyclic (x^N + 1) by
+ *   - the number theoretic transform (Sec. 2.3, Eq. 11) and its inverse, negacyclic (x^N + 1) by
  *     default or cyclic (x^N - 1).
  * Every result is the exact canonical residue in [0, q): the arithmetic is integer only.
  *
@@ -57,14 +57,14 @@ extern "C" {
 
 /* plan flags */
 #define MQ_NEGACYCLIC 0u    /* modulus x^N + 1; root = psi, a primitive 2N-th root of unity */
-#define MQ_CYCLIC 1u        /* modulus x^N - 1 (Eq. 4); root = w, a primitive N-th root of unity */
+#define MQ_CYCLIC 1u        /* modulus x^N - 1 (Eq. 11); root = w, a primitive N-th root of unity */
 #define MQ_ORDER_NATURAL 0u /* transformed side in natural order: position k holds yhat_k */
 #define MQ_ORDER_BITREV 2u  /* transformed side in bit-reversed order: position i holds yhat_brv(i) */
 
 typedef struct ntt_plan ntt_plan;
 
 /*
- * Create a transform plan for N = 2^log2n residues mod q (Sec. 2.3, Eq. 4).
+ * Create a transform plan for N = 2^log2n residues mod q (Sec. 2.3, Eq. 11).
  *   negacyclic (default): yhat_k = sum_j x_j psi^((2k+1) j) mod q, q = 1 mod 2N, root = psi with
  *                         psi^N = -1 (order exactly 2N);
  *   cyclic:               y_k = sum_j x_j w^(jk) mod q, q = 1 mod N, root = w with w^(N/2) = -1.

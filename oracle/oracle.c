@@ -12,7 +12,7 @@
  *
  *   Sec. 2.1, Eq. 1       ring operations c = a + b, a - b, ab mod q on Z_q
  *   Sec. 2.3              point-wise polynomial ops as BLAS (vector add/sub/multiply, axpy y = ax + y)
- *   Sec. 2.3, Eq. 4       n-point NTT y_k = sum_j x_j w^{jk} mod q (cyclic, natural order)
+ *   Sec. 2.3, Eq. 11      n-point NTT y_k = sum_j x_j w^{jk} mod q (cyclic, natural order)
  *   Sec. 2.3              schoolbook polynomial product
  *   Sec. 3.2 (last par.)  butterfly = one modular add, one modular sub, one modular mul;
  *                         log n stages of n/2 butterflies
@@ -249,7 +249,7 @@ int oracle_blas(int op, uint64_t *out, const uint64_t *a, const uint64_t *b, con
     return 0;
 }
 
-/* ---------------------------------------------------------------- NTT (Sec. 2.3, Eq. 4) */
+/* ---------------------------------------------------------------- NTT (Sec. 2.3, Eq. 11) */
 
 #define OR_CYCLIC 1u /* root is an N-th root w; otherwise a 2N-th root psi (negacyclic) */
 #define OR_BITREV 2u /* transformed side in bit-reversed order */
@@ -301,7 +301,7 @@ static void cyclic_transform(bn *A, unsigned log2n, const bn *w, const bn *Q, bn
 
 /*
  * In-place transform of one polynomial of N = 2^log2n residues.
- *   forward, cyclic:       y_k = sum_j x_j w^{jk}                         (Eq. 4)
+ *   forward, cyclic:       y_k = sum_j x_j w^{jk}                         (Eq. 11)
  *   forward, negacyclic:   y_k = sum_j x_j psi^{(2k+1) j}  = cyclic_{w=psi^2}(x_j psi^j)_k
  *   inverse, cyclic:       x_j = N^{-1} sum_k y_k w^{-jk}
  *   inverse, negacyclic:   x_j = N^{-1} psi^{-j} sum_k y_k psi^{-2jk}
@@ -379,7 +379,7 @@ int oracle_ntt(uint64_t *x, size_t batch, size_t stride, unsigned log2n, const u
 }
 
 /*
- * The same transforms straight from the definition, O(N^2), for small N (Eq. 4 and the negacyclic
+ * The same transforms straight from the definition, O(N^2), for small N (Eq. 11 and the negacyclic
  * reading above).  out must not alias x.  Flags as in oracle_ntt.
  * Pinned by: the worked example of Sec. 2.3 and the unit-vector closed forms.
  */

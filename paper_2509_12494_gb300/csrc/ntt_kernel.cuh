@@ -6,7 +6,7 @@
 // exponent), forward stage m uses entry m + i for butterfly group i, and the output comes out in
 // bit-reversed order.  The inverse runs the stages backwards with Gentleman-Sande butterflies
 // (u + v, (u - v) w^-1) on the table of psi^-brv(k) and folds N^-1 into the last stage.  The cyclic
-// transform of Eq. 4 uses the same kernels with the table w^brv'(k) (brv' over log2 N - 1 bits of
+// transform of Eq. 11 uses the same kernels with the table w^brv'(k) (brv' over log2 N - 1 bits of
 // k minus its leading power of two).
 //
 // Work decomposition (GB300-first, not the paper's AVX-512 Pease dataflow):

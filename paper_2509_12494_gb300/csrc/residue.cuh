@@ -5,7 +5,7 @@
 // arithmetic of Sec. 2.2: additions with carry and subtractions with borrow are PTX carry chains
 // (add.cc/addc, sub.cc/subc -- the GPU's native form of the adc/sbb instructions that MQX adds to
 // AVX-512, Table 2), and products use the widening multiply halves mul.lo/mul.hi fused into
-// mad.lo.cc/madc.hi.cc chains (schoolbook, Eq. 5).
+// mad.lo.cc/madc.hi.cc chains (schoolbook, Eq. 8).
 //
 // Modular operations (Sec. 2.1):
 //   add_mod / sub_mod   conditional correction (Eq. 2 and 3): one add (sub) chain, one trial
@@ -158,7 +158,7 @@ __device__ __forceinline__ void mul_wide32(uint32_t a, uint32_t b, uint32_t &lo,
     hi = (uint32_t)(p >> 32);
 }
 
-// Full 128 x 128 -> 256-bit schoolbook product (Eq. 5 on 32-bit words).  Each 32 x 32 -> 64 limb
+// Full 128 x 128 -> 256-bit schoolbook product (Eq. 8 on 32-bit words).  Each 32 x 32 -> 64 limb
 // product a_j b_i is added into a pair of consecutive columns (i + j, i + j + 1) by a mad.lo.cc /
 // madc.hi.cc pair, which the GPU executes as one wide multiply-add on an aligned register pair.
 // To keep every pair aligned the products are split by the parity of i + j: E holds the pairs

@@ -5,7 +5,7 @@ Each ``pin_*`` function takes an ``oracle.Oracle`` instance and raises ``Asserti
 oracle disagrees with:
   * the worked example of Sec. 2.3 (tests/golden/toy_ntt_q5.txt),
   * Python's own big integers (``%``, ``pow``) on random and limb-boundary operands,
-  * the O(N^2) definition of Eq. 4 (and its negacyclic reading) computed here with Python integers
+  * the O(N^2) definition of Eq. 11 (and its negacyclic reading) computed here with Python integers
     on tiny N,
   * closed forms (unit vectors, the all-ones vector), invariants (inverse(forward(x)) = x,
     linearity, the convolution theorem against the schoolbook product), field identities.
@@ -34,7 +34,7 @@ def brv(i: int, bits: int) -> int:
 
 
 def py_forward(x, q, root, cyclic):
-    """Eq. 4 (cyclic) or its negacyclic reading, straight from the sum, with Python integers."""
+    """Eq. 11 (cyclic) or its negacyclic reading, straight from the sum, with Python integers."""
     N = len(x)
     if cyclic:
         return [sum(x[j] * pow(root, j * k, q) for j in range(N)) % q for k in range(N)]
