@@ -84,12 +84,17 @@ KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "blas_ops.cuh",
 
 
 def kernel_sources_sha256() -> str:
-    """Hash of the sources that define the persistent kernel (to tell whether a profile is current)."""
+    """Hash of the code (comments and blank space removed) of the sources that define the persistent
+    kernel, to tell whether a profile is current."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2509_12494_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2509_12494_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 
