@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-blas", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--workload", default="uniform", choices=["uniform", "serve"],
+    p.add_argument("--workload", default="uniform", choices=["uniform", "serve", "int8-probe"],
                    help="uniform: the default line (uniform batch, plus BLAS and the uneven batch as extra blocks); "
                         "serve: the Poisson serving sweep")
     p.add_argument("--no-uneven", action="store_true")
@@ -446,6 +446,13 @@ def run_gpu(args, rank, world):
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
     if not args.no_uneven:
         out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args))
+    if width == 2:   # the two forms of the double-word product (Sec. 2.2, Eq. 8 and 9), multiply-bound
+        r_s, _ = M.mq_probe_mulmod_rate(M.MQ_MUL_SCHOOLBOOK, 2000, q, stream=sh)
+        r_k, _ = M.mq_probe_mulmod_rate(M.MQ_MUL_KARATSUBA, 2000, q, stream=sh)
+        out["product_forms"] = {"what": "general 124-bit modular products (Barrett) per second on register-resident "
+                                        "operands, schoolbook vs Karatsuba double-word product",
+                                "schoolbook_mulmod_per_s": r_s, "karatsuba_mulmod_per_s": r_k,
+                                "karatsuba_over_schoolbook": r_k / r_s}
     if not args.no_polymul:
         out["polymul"] = bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul,
                                        alu_peak, args)
@@ -783,6 +790,42 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "butterflies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_int8_probe(args):
+    """The tensor-core question for a limb-split NTT stage: the dense int8 GEMM rate of this GPU
+    (cuBLASLt through torch._int_mm, int8 x int8 -> int32), and the butterfly rate that rate would
+    bound a limb-split radix-16 stage to.  A 16-point transform over Z_q as a dense 16 x 16 product
+    on 8-bit limbs of 124-bit residues takes 16 x 16 limb pairs per coefficient product and 16 x 16
+    coefficient products per 16 outputs, which stand for 4 radix-2 stages of 8 butterflies: 2048
+    multiply-adds (4096 int8 operations) per butterfly, before the reductions mod q of the wide
+    accumulators, which run on the CUDA cores on top."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rates = {}
+    for n in (4096, 8192, 16384):
+        a = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+        b = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+        for _ in range(3):
+            torch._int_mm(a, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            torch._int_mm(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        rates[n] = 2 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3)
+        del a, b
+    ops = max(rates.values())
+    per_bfly = 2 * 16 * 16 * 16 * 16 / 32
+    return {"metric": METRIC, "workload": "int8-probe", "int8_ops_per_s": ops,
+            "by_size": {str(k): v for k, v in rates.items()}, "limb_split_int8_ops_per_butterfly": per_bfly,
+            "butterfly_bound_per_s": ops / per_bfly,
+            "note": "upper bound from the tensor part alone; the reductions mod q of the wide accumulators "
+                    "(CUDA cores) come on top"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -800,6 +843,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "serve":
         out = run_serve(args) if rank == 0 else None
+    elif args.workload == "int8-probe":
+        out = run_int8_probe(args) if rank == 0 else None
     else:
         out = run_gpu(args, rank, world)
         if out is not None and not args.no_cpu_baseline:

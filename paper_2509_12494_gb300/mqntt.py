@@ -65,6 +65,9 @@ def load(build_if_missing: bool = False):
         "mod_axpy": [_vp, _u64x2, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
         "mq_probe_imad_rate": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), _vp],
+        "mq_probe_mulmod": [ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _u64x2, _vp],
+        "mq_probe_mulmod_rate": [ctypes.c_int, ctypes.c_int, _u64x2, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), _vp],
         "mq_batch_create": [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _vp, _vp],
         "mq_batch_update": [_vp, _vp, ctypes.c_size_t, _vp],
         "mq_batch_launch": [_vp, _vp],
@@ -205,6 +208,22 @@ def mq_probe_imad_rate(kind: int, iters: int, stream=None):
     """(thread-instructions per second, kernel ms) of the multiply-add probe."""
     r, ms = ctypes.c_double(), ctypes.c_double()
     _check(load().mq_probe_imad_rate(kind, iters, ctypes.byref(r), ctypes.byref(ms), stream_handle(stream)))
+    return r.value, ms.value
+
+
+MQ_MUL_SCHOOLBOOK, MQ_MUL_KARATSUBA = 0, 1
+
+
+def mq_probe_mulmod(variant: int, c, a, b, n: int, q: int, stream=None):
+    """c = a * b mod q (124-bit residues) with the schoolbook or the Karatsuba double-word product."""
+    _check(load().mq_probe_mulmod(variant, ptr(c), ptr(a), ptr(b), n, words(q), stream_handle(stream)))
+
+
+def mq_probe_mulmod_rate(variant: int, iters: int, q: int, stream=None):
+    """(general 124-bit modular products per second, kernel ms) with the chosen product form."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().mq_probe_mulmod_rate(variant, iters, words(q), ctypes.byref(r), ctypes.byref(ms),
+                                       stream_handle(stream)))
     return r.value, ms.value
 
 
