@@ -223,11 +223,15 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
         const int half = 1 << (RR - 1 - j);  // distance in the register index
 #pragma unroll
         for (int k = 0; k < V; ++k) {
+            // twiddle index of butterfly (k, e0): (tw_base << s) + (l0 >> (L - s)) with
+            // l0 = base[k] | (e0 << b_lo); base[k] is zero in bits b_lo .. b_lo + RR - 1, so this is
+            // tb + (e0 >> (RR - j)), a compile-time offset: butterflies that share a twiddle share
+            // its load
+            const unsigned tb = (tw_base << s) + ((unsigned)base[k] >> (L - s));
 #pragma unroll
             for (int e0 = 0; e0 < (1 << RR); ++e0) {
                 if (e0 & half) continue;
-                const int l0 = base[k] | (e0 << b_lo);
-                const unsigned idx = (tw_base << s) + ((unsigned)l0 >> (L - s));
+                const unsigned idx = tb + (unsigned)(e0 >> (RR - j));
                 E &u = x[k * (1 << RR) + e0];
                 E &v = x[k * (1 << RR) + e0 + half];
                 E w, wp;
