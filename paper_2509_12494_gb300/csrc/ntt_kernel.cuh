@@ -200,7 +200,7 @@ __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned lon
 template <int W, int L, int RR, bool INV, int BAR = 0>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
                                             int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
-                                            typename Traits<W>::E q4, typename Traits<W>::E nq) {
+                                            typename Traits<W>::E q8, typename Traits<W>::E nq) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
     typedef Shape<W, L> S;
@@ -237,20 +237,20 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                 E w, wp;
                 if (!INV) {
                     Tr::load_tw(tw, idx, w, wp);
-                    E uu = csub(u, q4);                              // [0, 4q)
-                    E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 4q)
-                    u = add_nored(uu, tv);                           // [0, 8q)
-                    v = add_sub(uu, q4, tv);                         // (0, 8q)
+                    E uu = csub(u, q8);                              // [0, 8q)
+                    E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 6q)
+                    u = add_nored(uu, tv);                           // [0, 14q)
+                    v = add_sub(uu, q8, tv);                         // (2q, 16q)
                 } else if (s == 0 && a.scale) {
-                    E dif = add_sub(u, q4, v);                       // (0, 8q)
-                    E sum = add_nored(u, v);                         // [0, 8q)
+                    E dif = add_sub(u, q8, v);                       // (0, 16q)
+                    E sum = add_nored(u, v);                         // [0, 16q)
                     u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q, nq);
                     v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q, nq);
                 } else {
                     Tr::load_tw(tw, idx, w, wp);
-                    E dif = add_sub(u, q4, v);                       // (0, 8q)
-                    u = csub(add_nored(u, v), q4);                   // [0, 4q)
-                    v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 4q)
+                    E dif = add_sub(u, q8, v);                       // (0, 16q)
+                    u = csub(add_nored(u, v), q8);                   // [0, 8q)
+                    v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 6q)
                 }
             }
         }
@@ -273,7 +273,8 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
     typedef typename Tr::E E;
     typedef Shape<W, L> S;
     const E q = Tr::make(a.q);
-    const E q4 = add_nored(add_nored(q, q), add_nored(q, q));
+    const E q2 = add_nored(q, q), q4 = add_nored(q2, q2);
+    const E q8 = add_nored(q4, q4);
     const E nq = neg(q);
     const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
     const int g = tid / S::TPT, t = tid % S::TPT;
@@ -288,12 +289,12 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
     constexpr int FULL = L / S::r, PART = L - FULL * S::r;
     if (!INV) {
 #pragma unroll 1
-        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4, nq);
-        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4, nq);
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
+        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
     } else {
-        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q4, nq);
+        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
 #pragma unroll 1
-        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q4, nq);
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
     }
 }
 
@@ -302,12 +303,12 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
 // Called by NT = Shape::NT threads with thread index tid after a barrier that follows the staging;
 // ends with a barrier, after which `sm` may be refilled.
 //
-// Butterflies are lazy (after Harvey): between stages the values stay below 8q (forward) or 4q
-// (inverse), and twiddle products are left below 4q (Shoup without its final correction: [0, 4q)
+// Butterflies are lazy (after Harvey): between stages the values stay below 16q (forward) or 8q
+// (inverse), and twiddle products are left below 6q (Shoup without its final correction: [0, 6q)
 // at 128 bits, whose quotient comes from a truncated high product, [0, 2q) at 64 bits); the pass
-// flagged `final` canonicalises what it stores.  q < 2^124 (2^60) keeps 8q below the word size.
-//   forward (CT):  u <- u mod 4q;  t = w v mod q + {0, .., 3q};  (u, v) <- (u + t, u + 4q - t)
-//   inverse (GS):  (u, v) <- ((u + v) mod 4q, (u + 4q - v) w mod q + {0, .., 3q})
+// flagged `final` canonicalises what it stores.  q < 2^124 (2^60) keeps 16q below the word size.
+//   forward (CT):  u <- u mod 8q;  t = w v mod q + {0, .., 5q};  (u, v) <- (u + t, u + 8q - t)
+//   inverse (GS):  (u, v) <- ((u + v) mod 8q, (u + 8q - v) w mod q + {0, .., 5q})
 // Global loads and stores go through L2 only (.cg), so a pass may read what another SM wrote
 // earlier in the same kernel once the writer's completion is observed.
 template <int W, int L, bool INV, int BAR = 0>
@@ -320,6 +321,7 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
     const E q = Tr::make(a.q);
     const E q2 = add_nored(q, q);
     const E q4 = add_nored(q2, q2);
+    const E q8 = add_nored(q4, q4);
     const int L1 = a.L1, logN = a.logN;
     const TileAddr ta(a);
     const int lgTP = ta.lgTP;
@@ -339,7 +341,8 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
         if (poly < a.batch) {
             E v = sm[gg * S::TS + swz<W>(l)];
             if (a.final) {
-                if (!INV) v = csub(v, q4);  // forward values are below 8q, inverse ones below 4q
+                if (!INV) v = csub(v, q8);  // forward values are below 16q, inverse ones below 8q
+                v = csub(v, q4);
                 v = csub(v, q2);
                 v = csub(v, q);
             }

@@ -51,17 +51,18 @@ __global__ void __launch_bounds__(Shape<W, L>::NT, (Shape<W, L>::NT <= 256) ? 3 
         __syncthreads();
         ntt_detail::tile_rounds<W, L, false>(fa, first, ta, tid);
         ntt_detail::tile_rounds<W, L, false>(fb, first, tb, tid);
-        // pointwise product of the two spectra: canonical operands (forward values are below 8q),
+        // pointwise product of the two spectra: canonical operands (forward values are below 16q),
         // Barrett product, canonical result -- the same arithmetic as mod_vmul
         {
             const E q = Tr::make(fa.q);
             const E q2 = add_nored(q, q);
             const E q4 = add_nored(q2, q2);
+            const E q8 = add_nored(q4, q4);
             const typename ModOf<W>::M mod = ModOf<W>::make(m);
             for (int i = tid; i < S::G * S::T; i += S::NT) {
                 const int at = (i / S::T) * S::TS + ntt_detail::swz<W>(i % S::T);
-                const E x = csub(csub(csub(ta[at], q4), q2), q);
-                const E y = csub(csub(csub(tb[at], q4), q2), q);
+                const E x = csub(csub(csub(csub(ta[at], q8), q4), q2), q);
+                const E y = csub(csub(csub(csub(tb[at], q8), q4), q2), q);
                 ta[at] = mul_mod_barrett(x, y, mod);
             }
         }

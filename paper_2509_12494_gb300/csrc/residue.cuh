@@ -327,15 +327,14 @@ __device__ __forceinline__ uint4 mul_mod_shoup(uint4 a, uint4 w, uint4 wp, uint4
     return reduce_once(r, q);
 }
 
-// floor((a * b - D) / 2^128) where D = a0 b0 + 2^32 (a0 b1 + a1 b0) + 2^64 a2 b0 < 2^128 + 2^98:
-// the high half of the product without the four limb products a0 b0, a1 b0, a0 b1, a2 b0, which
-// reach columns 0..3 only.  Since D < 2 * 2^128 the result is the true high half minus 0, 1 or 2.
-// 12 limb products instead of 16, in the parity-split chains of mul_wide (the O pair (1,2) is
-// empty, and column 2 holds only E2, which carries nothing upward by itself).
+// floor((a * b - D) / 2^128) where D = sum of the limb products a_j b_i with i + j <= 2 (they reach
+// columns 0..3 only), D < 3 * 2^128 + 2^98: the true high half minus at most 4.  10 limb products
+// instead of 16, in the parity-split chains of mul_wide: O takes columns 3..7 from the products
+// with i + j = 3 and 5, E columns 4..7 from those with i + j = 4 and 6; column 3 holds only O3,
+// which carries nothing upward by itself.
 __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
-    uint32_t E2, E3, E4, E5, E6, E7, O3, O4, O5, O6, O7;
+    uint32_t E4, E5, E6, E7, O3, O4, O5, O6, O7;
     mul_wide32(a.w, b.x, O3, O4);  // a3 b0
-    mul_wide32(a.y, b.y, E2, E3);  // a1 b1
     mul_wide32(a.w, b.y, E4, E5);  // a3 b1
     // b1: a2 b1 -> O(3,4), carry -> O5
     asm("mad.lo.cc.u32  %0, %3, %4, %0;\n\t"
@@ -343,14 +342,12 @@ __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
         "addc.u32       %2, 0, 0;"
         : "+r"(O3), "+r"(O4), "=r"(O5)
         : "r"(a.z), "r"(b.y));
-    // b2: a0 b2 -> E(2,3), a2 b2 -> E(4,5), carry -> E6; a1 b2 -> O(3,4), a3 b2 -> O(5,6) (O6 new)
-    asm("mad.lo.cc.u32  %0, %5, %7, %0;\n\t"
-        "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
-        "madc.lo.cc.u32 %2, %6, %7, %2;\n\t"
-        "madc.hi.cc.u32 %3, %6, %7, %3;\n\t"
-        "addc.u32       %4, 0, 0;"
-        : "+r"(E2), "+r"(E3), "+r"(E4), "+r"(E5), "=r"(E6)
-        : "r"(a.x), "r"(a.z), "r"(b.z));
+    // b2: a2 b2 -> E(4,5), carry -> E6; a1 b2 -> O(3,4), a3 b2 -> O(5,6) (O6 new)
+    asm("mad.lo.cc.u32  %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32       %2, 0, 0;"
+        : "+r"(E4), "+r"(E5), "=r"(E6)
+        : "r"(a.z), "r"(b.z));
     asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
         "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
         "madc.lo.cc.u32 %2, %5, %6, %2;\n\t"
@@ -371,26 +368,24 @@ __device__ __forceinline__ uint4 mul_hi_trunc(const uint4 a, const uint4 b) {
         "addc.u32       %4, 0, 0;"
         : "+r"(O3), "+r"(O4), "+r"(O5), "+r"(O6), "=r"(O7)
         : "r"(a.x), "r"(a.z), "r"(b.w));
+    (void)O3;
     uint4 r;
-    uint32_t c3;
-    asm("add.cc.u32  %0, %5, %10;\n\t"
-        "addc.cc.u32 %1, %6, %11;\n\t"
-        "addc.cc.u32 %2, %7, %12;\n\t"
-        "addc.cc.u32 %3, %8, %13;\n\t"
-        "addc.u32    %4, %9, %14;"
-        : "=r"(c3), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "r"(E3), "r"(E4), "r"(E5), "r"(E6), "r"(E7), "r"(O3), "r"(O4), "r"(O5), "r"(O6), "r"(O7));
-    (void)c3;
+    asm("add.cc.u32  %0, %4, %8;\n\t"
+        "addc.cc.u32 %1, %5, %9;\n\t"
+        "addc.cc.u32 %2, %6, %10;\n\t"
+        "addc.u32    %3, %7, %11;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "r"(E4), "r"(E5), "r"(E6), "r"(E7), "r"(O4), "r"(O5), "r"(O6), "r"(O7));
     return r;
 }
 
-// a * w mod q up to three multiples of q: the result is in [0, 4q).  Shoup's quotient estimate is
-// the true quotient or one less, and the truncated high half takes at most two more away.  a may be
-// any value below 2^128 (lazy butterflies feed it values below 8q).  nq = 2^128 - q.
+// a * w mod q up to five multiples of q: the result is in [0, 6q).  Shoup's quotient estimate is
+// the true quotient or one less, and the truncated high half takes at most four more away.  a may
+// be any value below 2^128 (lazy butterflies feed it values below 16q).  nq = 2^128 - q.
 __device__ __forceinline__ uint4 mul_mod_shoup_lazy(uint4 a, uint4 w, uint4 wp, uint4 q, uint4 nq) {
     (void)q;
     uint4 qhat = mul_hi_trunc(a, wp);
-    return mul_lo2(a, w, qhat, nq);  // a w - qhat q mod 2^128, exact since it is < 4q < 2^126
+    return mul_lo2(a, w, qhat, nq);  // a w - qhat q mod 2^128, exact since it is < 6q < 2^127
 }
 
 // a >= m ? a - m : a
@@ -398,7 +393,7 @@ __device__ __forceinline__ uint4 csub(uint4 a, uint4 m) { return reduce_once(a, 
 
 __device__ __forceinline__ uint4 add_nored(uint4 a, uint4 b) { return add128(a, b); }
 
-// a + b2 - c for values that keep the result in [0, 2^128): b2 = 2q, c < 2q
+// a + b2 - c for values that keep the result in [0, 2^128): c <= a + b2
 __device__ __forceinline__ uint4 add_sub(uint4 a, uint4 b2, uint4 c) {
     return sub128(add128(a, b2), c);
 }
