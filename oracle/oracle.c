@@ -17,8 +17,11 @@
  *   Sec. 3.2 (last par.)  butterfly = one modular add, one modular sub, one modular mul;
  *                         log n stages of n/2 butterflies
  *
- * Residues are passed as arrays of 64-bit words: width 1 = one word per residue (q < 2^64),
- * width 2 = two words per residue, low word first (the memory order of an unsigned 128-bit value).
+ * Residues are passed as arrays of 64-bit words: width w = w words per residue, low word first
+ * (width 1: q < 2^64; width 2: the memory order of an unsigned 128-bit value).  Moduli and roots
+ * are arrays of max(w, 2) words.  The default build takes widths 1 and 2; the wide build
+ * (-DBN_LIMBS=18) also takes widths 3 and 4 (residues of 192 and 256 bits, the larger bit-widths
+ * of Sec. 7), with the same code on longer integers.
  *
  * Readings of the paper taken here (each one a choice where the paper is silent):
  *   - the negacyclic transform (modulus x^N + 1) with a primitive 2N-th root psi is
@@ -33,7 +36,11 @@
 #include <stdint.h>
 #include <string.h>
 
+#ifndef BN_LIMBS
 #define BN_LIMBS 10 /* 320 bits: a product of two values below 2^128 needs 8 limbs */
+#endif
+/* widths the build takes: a product of two values below 2^(64 w) needs 4 w limbs, plus one */
+#define MAX_WIDTH ((BN_LIMBS - 1) / 4)
 
 typedef struct {
     uint32_t l[BN_LIMBS]; /* little-endian 32-bit limbs */
@@ -41,19 +48,19 @@ typedef struct {
 
 /* ---------------------------------------------------------------- multi-precision integers */
 
-static void bn_set_words(bn *a, uint64_t lo, uint64_t hi) {
+/* a = the nw 64-bit words w[0..nw-1], low word first */
+static void bn_set_words(bn *a, const uint64_t *w, int nw) {
     memset(a, 0, sizeof *a);
-    a->l[0] = (uint32_t)lo;
-    a->l[1] = (uint32_t)(lo >> 32);
-    a->l[2] = (uint32_t)hi;
-    a->l[3] = (uint32_t)(hi >> 32);
+    for (int k = 0; k < nw; ++k) {
+        a->l[2 * k] = (uint32_t)w[k];
+        a->l[2 * k + 1] = (uint32_t)(w[k] >> 32);
+    }
 }
 
-static void bn_set_u64(bn *a, uint64_t v) { bn_set_words(a, v, 0); }
+static void bn_set_u64(bn *a, uint64_t v) { bn_set_words(a, &v, 1); }
 
-static void bn_get_words(const bn *a, uint64_t *lo, uint64_t *hi) {
-    *lo = (uint64_t)a->l[0] | ((uint64_t)a->l[1] << 32);
-    *hi = (uint64_t)a->l[2] | ((uint64_t)a->l[3] << 32);
+static void bn_get_words(const bn *a, uint64_t *w, int nw) {
+    for (int k = 0; k < nw; ++k) w[k] = (uint64_t)a->l[2 * k] | ((uint64_t)a->l[2 * k + 1] << 32);
 }
 
 static int bn_cmp(const bn *a, const bn *b) {
@@ -186,30 +193,24 @@ static void mod_pow_u64(bn *r, const bn *g, uint64_t e, const bn *q) {
 
 /* ---------------------------------------------------------------- element I/O */
 
-static void load_elem(bn *a, const uint64_t *p, size_t i, int width) {
-    if (width == 1)
-        bn_set_words(a, p[i], 0);
-    else
-        bn_set_words(a, p[2 * i], p[2 * i + 1]);
-}
+static void load_elem(bn *a, const uint64_t *p, size_t i, int width) { bn_set_words(a, p + (size_t)width * i, width); }
 
-static void store_elem(uint64_t *p, size_t i, const bn *a, int width) {
-    uint64_t lo, hi;
-    bn_get_words(a, &lo, &hi);
-    if (width == 1) {
-        p[i] = lo;
-    } else {
-        p[2 * i] = lo;
-        p[2 * i + 1] = hi;
-    }
-}
+static void store_elem(uint64_t *p, size_t i, const bn *a, int width) { bn_get_words(a, p + (size_t)width * i, width); }
 
-static int check_args(const uint64_t q[2], int width) {
-    if (width != 1 && width != 2) return -1;
+/* words of a modulus or root array: max(width, 2) */
+static int arg_words(int width) { return width < 2 ? 2 : width; }
+
+static int check_args(const uint64_t *q, int width) {
+    if (width < 1 || width > MAX_WIDTH) return -1;
     if (width == 1 && q[1] != 0) return -1;
-    if (q[1] == 0 && q[0] < 2) return -1;
+    int big = 0;
+    for (int k = 1; k < arg_words(width); ++k) big |= q[k] != 0;
+    if (!big && q[0] < 2) return -1;
     return 0;
 }
+
+/* The widest residue (in 64-bit words) this build takes: 2, or 4 for the wide build. */
+int oracle_max_width(void) { return MAX_WIDTH; }
 
 /* ---------------------------------------------------------------- BLAS (Sec. 2.3) */
 
@@ -226,10 +227,10 @@ enum { OR_VADD = 0, OR_VSUB = 1, OR_VMUL = 2, OR_AXPY = 3 };
  * Pinned by: Python integers on random and edge operands, and the field identities.
  */
 int oracle_blas(int op, uint64_t *out, const uint64_t *a, const uint64_t *b, const uint64_t *s,
-                size_t n, const uint64_t q[2], int width) {
+                size_t n, const uint64_t *q, int width) {
     if (check_args(q, width) || op < 0 || op > 3) return -1;
     bn Q, A, B, S, R;
-    bn_set_words(&Q, q[0], q[1]);
+    bn_set_words(&Q, q, arg_words(width));
     if (op == OR_AXPY) load_elem(&S, s, 0, width);
     for (size_t i = 0; i < n; ++i) {
         load_elem(&A, a, i, width);
@@ -364,14 +365,14 @@ static void ntt_one(uint64_t *x, unsigned log2n, const bn *Q, const bn *root, in
  */
 size_t oracle_ntt_work_bytes(unsigned log2n) { return sizeof(bn) * (((size_t)3 << log2n) / 2 + 1); }
 
-int oracle_ntt(uint64_t *x, size_t batch, size_t stride, unsigned log2n, const uint64_t q[2],
-               const uint64_t root[2], int width, unsigned flags, int inverse, void *work) {
+int oracle_ntt(uint64_t *x, size_t batch, size_t stride, unsigned log2n, const uint64_t *q,
+               const uint64_t *root, int width, unsigned flags, int inverse, void *work) {
     if (check_args(q, width) || log2n > 24 || !work) return -1;
     size_t N = (size_t)1 << log2n;
     if (batch > 1 && stride < N) return -1;
     bn Q, R;
-    bn_set_words(&Q, q[0], q[1]);
-    bn_set_words(&R, root[0], root[1]);
+    bn_set_words(&Q, q, arg_words(width));
+    bn_set_words(&R, root, arg_words(width));
     bn *A = (bn *)work, *pw = A + N;
     for (size_t b = 0; b < batch; ++b)
         ntt_one(x + b * stride * (size_t)width, log2n, &Q, &R, width, flags, inverse, A, pw);
@@ -383,16 +384,16 @@ int oracle_ntt(uint64_t *x, size_t batch, size_t stride, unsigned log2n, const u
  * reading above).  out must not alias x.  Flags as in oracle_ntt.
  * Pinned by: the worked example of Sec. 2.3 and the unit-vector closed forms.
  */
-int oracle_dft(uint64_t *out, const uint64_t *x, unsigned log2n, const uint64_t q[2],
-               const uint64_t root[2], int width, unsigned flags, int inverse) {
+int oracle_dft(uint64_t *out, const uint64_t *x, unsigned log2n, const uint64_t *q,
+               const uint64_t *root, int width, unsigned flags, int inverse) {
     if (check_args(q, width) || log2n > 12) return -1;
     size_t N = (size_t)1 << log2n;
     int cyclic = (flags & OR_CYCLIC) != 0;
     /* order of the root: N (cyclic) or 2N (negacyclic); exponents are reduced modulo it */
     size_t ord = cyclic ? N : 2 * N;
     bn Q, g, acc, term, xe, e, scale, N_bn;
-    bn_set_words(&Q, q[0], q[1]);
-    bn_set_words(&g, root[0], root[1]);
+    bn_set_words(&Q, q, arg_words(width));
+    bn_set_words(&g, root, arg_words(width));
     if (inverse) mod_inv(&g, &g, &Q);
     bn_set_u64(&N_bn, (uint64_t)N);
     mod_inv(&scale, &N_bn, &Q);
@@ -424,15 +425,15 @@ int oracle_dft(uint64_t *out, const uint64_t *x, unsigned log2n, const uint64_t 
  * Used to check single outputs of transforms too large for the full oracle.
  * `k` is the natural-order frequency index.
  */
-int oracle_ntt_point(uint64_t *out, const uint64_t *x, unsigned log2n, const uint64_t q[2],
-                     const uint64_t root[2], int width, unsigned flags, uint64_t k) {
+int oracle_ntt_point(uint64_t *out, const uint64_t *x, unsigned log2n, const uint64_t *q,
+                     const uint64_t *root, int width, unsigned flags, uint64_t k) {
     if (check_args(q, width) || log2n > 30) return -1;
     size_t N = (size_t)1 << log2n;
     if (k >= N) return -1;
     int cyclic = (flags & OR_CYCLIC) != 0;
     bn Q, g, step, pw, acc, xe, term;
-    bn_set_words(&Q, q[0], q[1]);
-    bn_set_words(&g, root[0], root[1]);
+    bn_set_words(&Q, q, arg_words(width));
+    bn_set_words(&g, root, arg_words(width));
     mod_pow_u64(&step, &g, cyclic ? k : 2 * k + 1, &Q);
     bn_set_u64(&pw, 1);
     bn_set_u64(&acc, 0);
@@ -452,15 +453,15 @@ int oracle_ntt_point(uint64_t *out, const uint64_t *x, unsigned log2n, const uin
  *   negacyclic:  x_j = N^{-1} sum_k y_k psi^{-(2k+1) j}
  * `y` in natural order; `j` the coefficient index.
  */
-int oracle_intt_point(uint64_t *out, const uint64_t *y, unsigned log2n, const uint64_t q[2],
-                      const uint64_t root[2], int width, unsigned flags, uint64_t j) {
+int oracle_intt_point(uint64_t *out, const uint64_t *y, unsigned log2n, const uint64_t *q,
+                      const uint64_t *root, int width, unsigned flags, uint64_t j) {
     if (check_args(q, width) || log2n > 30) return -1;
     size_t N = (size_t)1 << log2n;
     if (j >= N) return -1;
     int cyclic = (flags & OR_CYCLIC) != 0;
     bn Q, g, gi, step, base, pw, acc, ye, term, N_bn, ninv;
-    bn_set_words(&Q, q[0], q[1]);
-    bn_set_words(&g, root[0], root[1]);
+    bn_set_words(&Q, q, arg_words(width));
+    bn_set_words(&g, root, arg_words(width));
     mod_inv(&gi, &g, &Q);
     /* term k uses gi^{jk} (cyclic) or gi^{(2k+1)j} = gi^j * (gi^{2j})^k (negacyclic) */
     if (cyclic) {
@@ -492,11 +493,11 @@ int oracle_intt_point(uint64_t *out, const uint64_t *y, unsigned log2n, const ui
  * Pinned by: hand-computed small products, x^{N-1} * x = -1, commutativity, and the identity.
  */
 int oracle_negacyclic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, unsigned log2n,
-                          const uint64_t q[2], int width) {
+                          const uint64_t *q, int width) {
     if (check_args(q, width) || log2n > 14) return -1;
     size_t N = (size_t)1 << log2n;
     bn Q, acc, ai, bj, p;
-    bn_set_words(&Q, q[0], q[1]);
+    bn_set_words(&Q, q, arg_words(width));
     for (size_t k = 0; k < N; ++k) {
         bn_set_u64(&acc, 0);
         for (size_t i = 0; i < N; ++i) {
@@ -523,10 +524,10 @@ int oracle_negacyclic_mul(uint64_t *out, const uint64_t *a, const uint64_t *b, u
 int oracle_powmod(uint64_t *out, const uint64_t g[2], const uint64_t e[2], const uint64_t q[2]) {
     if (q[1] == 0 && q[0] < 2) return -1;
     bn G, E, Q, R;
-    bn_set_words(&G, g[0], g[1]);
-    bn_set_words(&E, e[0], e[1]);
-    bn_set_words(&Q, q[0], q[1]);
+    bn_set_words(&G, g, 2);
+    bn_set_words(&E, e, 2);
+    bn_set_words(&Q, q, 2);
     mod_pow(&R, &G, &E, &Q);
-    bn_get_words(&R, &out[0], &out[1]);
+    bn_get_words(&R, out, 2);
     return 0;
 }

@@ -87,10 +87,32 @@ def gen_root(q: int, log2n: int, seed: int, cyclic: bool = False) -> int:
 
 
 def gen_residues(n: int, q: int, seed: int, width: int | None = None) -> np.ndarray:
-    """n residues uniform in [0, q) (numpy PCG64, rejection sampling on bitlen(q)-bit draws)."""
+    """n residues uniform in [0, q) (numpy PCG64, rejection sampling on bitlen(q)-bit draws).
+    Shape (n,) for width 1, (n, width) -- low word first -- otherwise."""
     width = width or (1 if q < 2**64 else 2)
     bits = q.bit_length()
     rng = np.random.Generator(np.random.PCG64(seed))
+    if width > 2:
+        if q >= 1 << (64 * width):
+            raise ValueError("q too large for the width")
+        qw = [np.uint64((q >> (64 * k)) & (2**64 - 1)) for k in range(width)]
+        top = width - 1
+        tbits = min(max(bits - 64 * top, 0), 64)
+        tmask = np.uint64((1 << tbits) - 1) if tbits < 64 else np.uint64(2**64 - 1)
+        out = np.zeros((n, width), dtype=np.uint64)
+        todo = np.arange(n)
+        while todo.size:
+            draw = [rng.bit_generator.random_raw(todo.size).astype(np.uint64) for _ in range(width)]
+            draw[top] &= tmask
+            less = np.zeros(todo.size, dtype=bool)   # draw < q, decided from the top word down
+            equal = np.ones(todo.size, dtype=bool)
+            for k in range(top, -1, -1):
+                less |= equal & (draw[k] < qw[k])
+                equal &= draw[k] == qw[k]
+            for k in range(width):
+                out[todo[less], k] = draw[k][less]
+            todo = todo[~less]
+        return out
     if width == 1:
         if q >= 2**64:
             raise ValueError("q too large for width 1")
@@ -121,19 +143,22 @@ def gen_residues(n: int, q: int, seed: int, width: int | None = None) -> np.ndar
 
 
 def to_ints(a: np.ndarray) -> list[int]:
-    """Residue array -> Python ints (for checks on small arrays)."""
+    """Residue array -> Python ints (for checks on small arrays); the last axis holds the words of
+    a residue unless the array is one-dimensional (width 1)."""
     if a.ndim == 1:
         return [int(v) for v in a]
-    return [int(lo) | (int(hi) << 64) for lo, hi in a.reshape(-1, 2)]
+    w = a.shape[-1]
+    return [sum(int(x) << (64 * k) for k, x in enumerate(r)) for r in a.reshape(-1, w)]
 
 
 def from_ints(vals, width: int) -> np.ndarray:
     vals = [int(v) for v in vals]
     if width == 1:
         return np.array(vals, dtype=np.uint64)
-    return np.array([[v & (2**64 - 1), v >> 64] for v in vals], dtype=np.uint64).reshape(-1, 2)
+    return np.array([[(v >> (64 * k)) & (2**64 - 1) for k in range(width)] for v in vals],
+                    dtype=np.uint64).reshape(-1, width)
 
 
-def words(v: int) -> tuple[int, int]:
-    """A residue or modulus as (low word, high word)."""
-    return v & (2**64 - 1), v >> 64
+def words(v: int, n: int = 2) -> tuple[int, ...]:
+    """A residue or modulus as n 64-bit words, low word first."""
+    return tuple((v >> (64 * k)) & (2**64 - 1) for k in range(n))

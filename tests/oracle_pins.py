@@ -76,8 +76,15 @@ def _largest_prime(bits: int, m: int) -> int:
 
 
 @functools.lru_cache(maxsize=None)
-def moduli():
-    """(q, width, max log2 of a negacyclic size) for small, 60-bit, 64-bit and 124-bit primes."""
+def moduli(max_width: int = 2):
+    """(q, width, max log2 of a negacyclic size) for small, 60-bit, 64-bit and 124-bit primes, and
+    for a build that takes them, 188-bit (three words) and 252-bit (four words) primes."""
+    wide = [
+        (W.gen_prime(188, 18, 15), 3, 12),
+        (W.gen_prime(252, 18, 16), 4, 12),
+        (_largest_prime(252, 18), 4, 12),
+        (W.gen_prime(160, 18, 17), 3, 12),
+    ] if max_width >= 4 else []
     return [
         (17, 1, 3),
         (97, 1, 4),
@@ -88,12 +95,13 @@ def moduli():
         (W.gen_prime(124, 18, 13), 2, 17),
         (_largest_prime(124, 18), 2, 17),
         (W.gen_prime(90, 18, 14), 2, 17),
-    ]
+    ] + wide
 
 
 def edge_operands(q: int):
     cands = [0, 1, 2, q - 1, q - 2, (q - 1) // 2, (q + 1) // 2, 2**32 - 1, 2**32, 2**63, 2**64 - 1, 2**64,
-             2**64 + 1, 2**96 - 1, 2**96, 2**123]
+             2**64 + 1, 2**96 - 1, 2**96, 2**123, 2**128 - 1, 2**128, 2**160, 2**187, 2**192 - 1, 2**192, 2**224,
+             2**251]
     return sorted({c for c in cands if 0 <= c < q})
 
 
@@ -139,7 +147,7 @@ def pin_toy_example(O):
 def pin_blas_python_ints(O):
     """Each BLAS op against Python's exact integers on edge and random operands (Sec. 2.1, Eq. 1)."""
     rnd = random.Random(1)
-    for q, width, _ in moduli():
+    for q, width, _ in moduli(O.max_width):
         e = edge_operands(q)
         a = [x for x in e for _ in e] + [rnd.randrange(q) for _ in range(64)]
         b = [y for _ in e for y in e] + [rnd.randrange(q) for _ in range(64)]
@@ -154,7 +162,7 @@ def pin_blas_python_ints(O):
 def pin_blas_identities(O):
     """Field identities of Z_q for the BLAS ops."""
     rnd = random.Random(2)
-    for q, width, _ in moduli():
+    for q, width, _ in moduli(O.max_width):
         n = 48
         a = [rnd.randrange(q) for _ in range(n)]
         b = [rnd.randrange(q) for _ in range(n)]
@@ -179,9 +187,9 @@ def pin_blas_identities(O):
         assert ints(mul(qm1, qm1)) == [1]
 
 
-def _ntt_cases():
+def _ntt_cases(O):
     rnd = random.Random(3)
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         for log2n in range(1, min(maxlog, 5) + 1):
             for cyclic in (False, True):
                 root = W.gen_root(q, log2n, seed=log2n, cyclic=cyclic)
@@ -190,7 +198,7 @@ def _ntt_cases():
 
 def pin_ntt_bruteforce(O):
     """Fast oracle NTT (both kinds, both orders, both directions) against the O(N^2) sum."""
-    for q, width, log2n, cyclic, root, rnd in _ntt_cases():
+    for q, width, log2n, cyclic, root, rnd in _ntt_cases(O):
         N = 1 << log2n
         x = [rnd.randrange(q) for _ in range(N)]
         ref = py_forward(x, q, root, cyclic)
@@ -205,7 +213,7 @@ def pin_ntt_bruteforce(O):
 
 def pin_dft_bruteforce(O):
     """The oracle's O(N^2) routine against the same sum written with Python integers."""
-    for q, width, log2n, cyclic, root, rnd in _ntt_cases():
+    for q, width, log2n, cyclic, root, rnd in _ntt_cases(O):
         if log2n > 4:
             continue
         N = 1 << log2n
@@ -220,7 +228,7 @@ def pin_dft_bruteforce(O):
 
 def pin_closed_forms(O):
     """Unit vectors and the all-ones vector, whose transforms have closed forms."""
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         for log2n in sorted({min(maxlog, 3), min(maxlog, 6), min(maxlog, 10)}):
             N = 1 << log2n
             psi = W.gen_root(q, log2n, seed=7)
@@ -244,7 +252,7 @@ def pin_closed_forms(O):
 def pin_roundtrip_and_linearity(O):
     """inverse(forward(x)) = x in both orders; forward(a + c*b) = forward(a) + c*forward(b)."""
     rnd = random.Random(4)
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         log2n = min(maxlog, 9)
         N = 1 << log2n
         psi = W.gen_root(q, log2n, seed=9)
@@ -262,7 +270,7 @@ def pin_roundtrip_and_linearity(O):
 def pin_convolution(O):
     """Convolution theorem: inverse(forward(a) . forward(b)) = schoolbook product mod x^N + 1."""
     rnd = random.Random(5)
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         for log2n in sorted({min(maxlog, 4), min(maxlog, 7)}):
             N = 1 << log2n
             psi = W.gen_root(q, log2n, seed=10)
@@ -281,7 +289,7 @@ def pin_negacyclic_mul(O):
     # (1 + 2x)(x^2 + x^3) = x^2 + 3x^3 + 2x^4 = -2 + x^2 + 3x^3 mod (x^4 + 1, 17)
     assert ints(O.negacyclic_mul(arr([1, 2, 0, 0], 1), arr([0, 0, 1, 1], 1), 2, 17, 1)) == [15, 0, 1, 3]
     rnd = random.Random(6)
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         log2n = min(maxlog, 5)
         N = 1 << log2n
         top, x1 = [0] * (N - 1) + [1], [0, 1] + [0] * (N - 2)
@@ -297,7 +305,7 @@ def pin_negacyclic_mul(O):
 def pin_points(O):
     """Single-output routines against the Python sum (small N) and against the pinned fast NTT."""
     rnd = random.Random(7)
-    for q, width, maxlog in moduli():
+    for q, width, maxlog in moduli(O.max_width):
         log2n = min(maxlog, 5)
         N = 1 << log2n
         for cyclic in (False, True):
@@ -320,13 +328,13 @@ def pin_points(O):
 
 def pin_batched_stride(O):
     """A batch with a stride larger than N transforms each polynomial alone and skips the gaps."""
-    for q, width, maxlog in moduli()[3:]:
+    for q, width, maxlog in moduli(O.max_width)[3:]:
         log2n, batch = 4, 3
         N = 1 << log2n
         stride = N + 5
         psi = W.gen_root(q, log2n, seed=14)
         flat = W.gen_residues(batch * stride, q, seed=15, width=width)
-        x = flat.reshape((batch, stride) if width == 1 else (batch, stride, 2)).copy()
+        x = flat.reshape((batch, stride) if width == 1 else (batch, stride, width)).copy()
         ref = [ints(O.ntt(x[b, :N].copy(), log2n, q, psi, width)) for b in range(batch)]
         xb = O.ntt_strided(flat, batch, stride, log2n, q, psi, width).reshape(x.shape)
         for b in range(batch):
@@ -336,7 +344,9 @@ def pin_batched_stride(O):
 
 def pin_powmod(O):
     rnd = random.Random(8)
-    for q, width, _ in moduli():
+    for q, width, _ in moduli(O.max_width):
+        if width > 2:
+            continue  # oracle_powmod takes two-word operands
         for _ in range(8):
             g, e = rnd.randrange(q), rnd.randrange(2**128)
             assert O.powmod(g, e, q) == pow(g, e, q)

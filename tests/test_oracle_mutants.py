@@ -41,7 +41,8 @@ MUTANTS = {
                                    "mod_pow_u64(&step, &g, cyclic ? k : 2 * k, &Q);"),
     "negacyclic_fold_sign": ("                mod_sub(&acc, &acc, &p, &Q);", "                mod_add(&acc, &acc, &p, &Q);"),
     "pow_skips_multiply": ("if (bn_bit(e, i)) mod_mul(&acc, &acc, &base, q);", "if (bn_bit(e, i) && i) mod_mul(&acc, &acc, &base, q);"),
-    "high_word_lost_on_load": ("bn_set_words(a, p[2 * i], p[2 * i + 1]);", "bn_set_words(a, p[2 * i], 0);"),
+    "high_word_lost_on_load": ("bn_set_words(a, p + (size_t)width * i, width);",
+                               "bn_set_words(a, p + (size_t)width * i, 1);"),
 }
 
 RUNNER = textwrap.dedent("""

@@ -5,9 +5,11 @@ import oracle
 from tests import oracle_pins
 
 
-@pytest.fixture(scope="module")
-def O():
-    return oracle.default()
+@pytest.fixture(scope="module", params=["default", "wide"])
+def O(request):
+    """Both builds of the oracle: widths 1-2, and the wide one (widths 1-4, pinned on 188- and 252-bit
+    primes as well)."""
+    return oracle.default() if request.param == "default" else oracle.wide()
 
 
 @pytest.mark.parametrize("pin", oracle_pins.PINS, ids=[p.__name__ for p in oracle_pins.PINS])

@@ -57,13 +57,14 @@ def test_gen_root_order(log2n):
         W.gen_root(97, 10, seed=0)  # 2048 does not divide 96
 
 
-@pytest.mark.parametrize("bits,width", [(60, 1), (64, 1), (124, 2), (90, 2), (65, 2), (17, 1)])
+@pytest.mark.parametrize("bits,width", [(60, 1), (64, 1), (124, 2), (90, 2), (65, 2), (17, 1), (188, 3), (150, 3),
+                                        (252, 4), (200, 4)])
 def test_gen_residues_range_and_determinism(bits, width):
     q = W.gen_prime(bits, min(bits - 2, 10), 5)
     a = W.gen_residues(10000, q, seed=9, width=width)
     b = W.gen_residues(10000, q, seed=9, width=width)
     assert np.array_equal(a, b)
-    assert a.shape == ((10000,) if width == 1 else (10000, 2))
+    assert a.shape == ((10000,) if width == 1 else (10000, width))
     vals = W.to_ints(a)
     assert max(vals) < q and min(vals) >= 0
     # roughly uniform: the mean of v/q is near 1/2 and both halves of [0, q) are hit
@@ -75,4 +76,7 @@ def test_gen_residues_range_and_determinism(bits, width):
 def test_int_round_trip():
     vals = [0, 1, 2**64 - 1, 2**64, 2**124 - 3]
     assert W.to_ints(W.from_ints(vals, 2)) == vals
+    wide = vals + [2**128, 2**191 + 5, 2**255 + 2**64 + 1]
+    assert W.to_ints(W.from_ints(wide, 4)) == wide
+    assert W.to_ints(W.from_ints(wide[:-1], 3)) == wide[:-1]
     assert W.to_ints(W.from_ints([0, 5, 2**64 - 1], 1)) == [0, 5, 2**64 - 1]
