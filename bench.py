@@ -54,6 +54,7 @@ def parse():
                         "serve: the Poisson serving sweep")
     p.add_argument("--no-uneven", action="store_true")
     p.add_argument("--no-polymul", action="store_true")
+    p.add_argument("--no-wide", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=1.5)
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
@@ -453,12 +454,42 @@ def run_gpu(args, rank, world):
                                         "operands, schoolbook vs Karatsuba double-word product",
                                 "schoolbook_mulmod_per_s": r_s, "karatsuba_mulmod_per_s": r_k,
                                 "karatsuba_over_schoolbook": r_k / r_s}
+    if not args.no_wide:
+        out["wide"] = bench_wide(M, torch, dev, sh, timed, args)
     if not args.no_polymul:
         out["polymul"] = bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul,
                                        alu_peak, args)
 
     out["clocks"] = clocks
     return out
+
+
+def bench_wide(M, torch, dev, sh, timed, args):
+    """Residues of three and four 64-bit words (192- and 256-bit q, the larger bit-widths of Sec. 7):
+    forward + inverse transform of 64 polynomials of N = 2^16, one call per direction, bit-exact
+    round trip checked."""
+    from paper_2509_12494_gb300 import workload as W
+    res = {}
+    batch, log2n = 64, 16
+    N = 1 << log2n
+    for width, bits in ((3, 188), (4, 252)):
+        q = W.gen_prime(bits, 18, 1)
+        plan = M.ntt_plan_create(log2n, q, W.gen_root(q, log2n, 1), width, M.MQ_ORDER_BITREV, stream=sh)
+        d = M.to_device(W.gen_residues(batch * N, q, seed=width, width=width), dev)
+        x0 = d.clone()
+
+        def step():
+            M.ntt_forward(plan, d, batch, N, stream=sh)
+            M.ntt_inverse(plan, d, batch, N, stream=sh)
+
+        ms = statistics.median(timed(step, args.steps, args.warmup))
+        torch.cuda.synchronize()
+        bfly = 2 * batch * (N // 2) * log2n
+        res[f"w{64 * width}"] = {"q_bits": bits, "ms_per_step": ms, "butterflies_per_s": bfly / (ms * 1e-3),
+                                 "roundtrip_bit_exact": bool(torch.equal(d, x0))}
+        del d, x0, plan
+    res["workload"] = f"{batch} x N=2^{log2n} negacyclic forward+inverse per width, bit-reversed order"
+    return res
 
 
 def bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul, alu_peak, args):

@@ -18,15 +18,18 @@
  *   - Residues: width MQ_W64 stores one residue per 64-bit word (q < 2^60); width MQ_W128 stores one
  *     residue per two 64-bit words, low word first (the memory image of an unsigned 128-bit
  *     integer; q < 2^124, the 124-bit bound of Sec. 2.1 that keeps Barrett's constant in range).
- *     Moduli and scalars are passed as two 64-bit words, low first; for MQ_W64 the high word
- *     must be 0.
+ *     Widths MQ_W192 and MQ_W256 store three and four words (q < 2^188, q < 2^252), the larger
+ *     bit-widths of Sec. 7; they take the transforms (N <= 2^20) and the BLAS ops, not the fused
+ *     product, the batched form or the server.  Moduli, roots and scalars are passed as
+ *     max(width, 2) 64-bit words, low first; for MQ_W64 the high word must be 0.
  *   - q must be odd and at least 3.  Primality is the caller's responsibility for the NTT (the
  *     plan checks the root's order, which needs a field to mean anything); the BLAS ops are exact
  *     for any odd q.
  *   - Inputs must be canonical (< q); non-canonical inputs give unspecified (but memory-safe)
  *     results.
  *   - Device pointers are caller-owned device memory (for example torch tensors) and must be
- *     aligned to the residue size (8 or 16 bytes); MQ_ERR_ALIGN otherwise.
+ *     aligned to the residue size (8, 16, 8 and 32 bytes for widths 1 to 4); MQ_ERR_ALIGN
+ *     otherwise.
  */
 #ifndef MQNTT_H
 #define MQNTT_H
@@ -54,6 +57,8 @@ extern "C" {
 /* residue widths */
 #define MQ_W64 1  /* uint64_t residues, q < 2^60 */
 #define MQ_W128 2 /* {lo, hi} uint64_t pairs, q < 2^124 */
+#define MQ_W192 3 /* three uint64_t words, low first, q < 2^188 (transforms up to N = 2^20) */
+#define MQ_W256 4 /* four uint64_t words, low first, q < 2^252 (transforms up to N = 2^20) */
 
 /* plan flags */
 #define MQ_NEGACYCLIC 0u    /* modulus x^N + 1; root = psi, a primitive 2N-th root of unity */

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "hostmath.h"
 #include "plan.h"
+#include "widehost.h"
 
 using namespace mq;
 
@@ -44,7 +45,7 @@ extern "C" const char *mq_version(void) { return "mqntt 0.1 (sm_103a)"; }
 
 int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv) {
     if (!q) return mq_fail(MQ_ERR_ARG, "q is NULL");
-    if (width != MQ_W64 && width != MQ_W128) return mq_fail(MQ_ERR_ARG, "width must be MQ_W64 or MQ_W128, got %d", width);
+    if (width != MQ_W64 && width != MQ_W128) return mq_fail(MQ_ERR_ARG, "width must be MQ_W64 or MQ_W128 here, got %d", width);
     hm::u128 v = hm::from_words(q);
     if (v < 3 || (v & 1) == 0) return mq_fail(MQ_ERR_MODULUS, "q must be odd and >= 3");
     if (width == MQ_W64 && (q[1] != 0 || hm::bitlen(v) > 60)) return mq_fail(MQ_ERR_MODULUS, "MQ_W64 needs q < 2^60");
@@ -53,9 +54,23 @@ int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv) {
     return MQ_OK;
 }
 
+// alignment a residue array needs: its vector loads (one word for 192-bit residues)
+static unsigned align_of(int width) { return width == 3 ? 8u : 8u * (unsigned)width; }
+
 static int check_ptr(const void *p, int width, const char *name) {
     if (!p) return mq_fail(MQ_ERR_ARG, "%s is NULL", name);
-    if (((uintptr_t)p) % (8u * (unsigned)width)) return mq_fail(MQ_ERR_ALIGN, "%s is not %d-byte aligned", name, 8 * width);
+    if (((uintptr_t)p) % align_of(width)) return mq_fail(MQ_ERR_ALIGN, "%s is not %u-byte aligned", name, align_of(width));
+    return MQ_OK;
+}
+
+// residues of three and four words: q odd, 3 <= q < 2^(64 width - 4), so that 16q fits the word
+static int check_modulus_wide(const uint64_t *q, int width, hw::U *qv) {
+    if (!q) return mq_fail(MQ_ERR_ARG, "q is NULL");
+    hw::U v = hw::from_words(q, width);
+    if (hw::cmp(v, hw::from_u64(3)) < 0 || (v.w[0] & 1) == 0) return mq_fail(MQ_ERR_MODULUS, "q must be odd and >= 3");
+    if (hw::bitlen(v) > 64 * width - 4)
+        return mq_fail(MQ_ERR_MODULUS, "width %d needs q < 2^%d", width, 64 * width - 4);
+    *qv = v;
     return MQ_OK;
 }
 
@@ -107,6 +122,64 @@ int mq_pool_free(void *p, cudaStream_t s) {
 
 static int split_of(unsigned log2n) { return log2n <= 12 ? 0 : (int)(log2n / 2); }
 
+// wide residues: tiles of up to 2^10 (four residues per thread), so N <= 2^20
+static int split_of_wide(unsigned log2n) { return log2n <= 10 ? 0 : (int)(log2n / 2); }
+
+static int plan_create_wide(ntt_plan **out, unsigned log2n, const uint64_t *q, const uint64_t *root, int width,
+                            unsigned flags, cudaStream_t s) {
+    if (log2n > 20) return mq_fail(MQ_ERR_SIZE, "residues of %d words need log2n <= 20, got %u", width, log2n);
+    hw::U Q;
+    int rc = check_modulus_wide(q, width, &Q);
+    if (rc) return rc;
+    const int cyclic = (flags & MQ_CYCLIC) != 0;
+    const unsigned lord = log2n + (cyclic ? 0 : 1);  // log2 of the root's order
+    const hw::U Qm1 = hw::sub(Q, hw::from_u64(1));
+    if (Qm1.w[0] & ((1ull << lord) - 1)) return mq_fail(MQ_ERR_MODULUS, "q - 1 is not divisible by %s", cyclic ? "N" : "2N");
+    const hw::U r = hw::from_words(root, width);
+    if (hw::bitlen(r) == 0 || hw::cmp(r, Q) >= 0) return mq_fail(MQ_ERR_ROOT, "root must be in [1, q)");
+    if (hw::cmp(hw::powmod(r, 1ull << (lord - 1), Q), Qm1) != 0)
+        return mq_fail(MQ_ERR_ROOT, "root is not a primitive %s root of unity", cyclic ? "N-th" : "2N-th");
+
+    ntt_plan *p = new ntt_plan();
+    memset(p, 0, sizeof *p);
+    cudaGetDevice(&p->device);
+    p->log2n = log2n;
+    p->width = width;
+    p->flags = flags;
+    p->L = hw::bitlen(Q);
+    hw::to_words(Q, p->q, width);
+    hw::to_words(hw::barrett_mu(Q, p->L), p->mu, width);
+    hw::to_words(r, p->root, width);
+    const hw::U rinv = hw::powmod(r, (1ull << lord) - 1, Q);
+    hw::to_words(rinv, p->root_inv, width);
+    const int B = 64 * width;
+    const hw::U ninv = hw::sub(Q, hw::shr(Qm1, (int)log2n));  // q - (q - 1) / N: N times it is 1 mod q
+    const hw::U t1 = cyclic ? hw::from_u64(1) : hw::powmod(rinv, 1ull << (log2n - 1), Q);  // inverse-table entry 1
+    const hw::U ws = hw::mulmod(t1, ninv, Q);
+    hw::to_words(ninv, p->sc, width);
+    hw::to_words(hw::shoup(ninv, Q, B), p->scp, width);
+    hw::to_words(ws, p->ws, width);
+    hw::to_words(hw::shoup(ws, Q, B), p->wsp, width);
+    p->L1 = split_of_wide(log2n);
+
+    size_t bytes = ((size_t)1 << log2n) * 16u * (size_t)width;
+    cudaError_t e = cudaMalloc(&p->tw_fwd, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tw_inv, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ntt_plan_destroy(p);
+        return mq_fail(MQ_ERR_OOM, "twiddle tables (%zu bytes) do not fit", 2 * bytes);
+    }
+    e = launch_twiddle_build(width, (int)log2n, cyclic, p->q, p->root, p->root_inv, p->mu, p->L, p->tw_fwd, p->tw_inv, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ntt_plan_destroy(p);
+        return mq_cuda_fail(e, "twiddle build");
+    }
+    *out = p;
+    return MQ_OK;
+}
+
 extern "C" int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[2], const uint64_t root[2], int width,
                                unsigned flags, void *stream) {
     if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
@@ -114,6 +187,8 @@ extern "C" int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[
     if (!root) return mq_fail(MQ_ERR_ARG, "root is NULL");
     if (flags & ~(MQ_CYCLIC | MQ_ORDER_BITREV)) return mq_fail(MQ_ERR_ARG, "unknown flag bits 0x%x", flags);
     if (log2n < 1 || log2n > 24) return mq_fail(MQ_ERR_SIZE, "log2n must be in [1, 24], got %u", log2n);
+    if (width == MQ_W192 || width == MQ_W256)
+        return plan_create_wide(out, log2n, q, root, width, flags, (cudaStream_t)stream);
     hm::u128 Q;
     int rc = mq_check_modulus(q, width, &Q);
     if (rc) return rc;
@@ -214,7 +289,7 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
     const size_t N = (size_t)1 << p->log2n;
     if (batch == 1) stride = N;
     if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
-    if (batch > (SIZE_MAX / 16) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
+    if (batch > (SIZE_MAX / 32) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
     cudaStream_t s = (cudaStream_t)stream;
     const bool natural = !(p->flags & MQ_ORDER_BITREV);
     const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
@@ -296,6 +371,7 @@ extern "C" int ntt_inverse(const ntt_plan *p, void *d, size_t batch, size_t stri
 extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void *b, size_t batch, size_t stride,
                            void *stream) {
     if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
+    if (p->width > MQ_W128) return mq_fail(MQ_ERR_ARG, "the fused product takes residues of one or two words");
     if (batch == 0) return MQ_OK;
     int rc;
     if ((rc = check_ptr(c, p->width, "d_c")) || (rc = check_ptr(a, p->width, "d_a")) ||
@@ -370,8 +446,39 @@ extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void
 // BLAS
 // ------------------------------------------------------------------------------------------------
 
+static int blas_wide(int op, void *c, const void *a, const void *b, size_t n, const uint64_t *q, int width,
+                     const uint64_t *scalar, void *stream) {
+    hw::U Q;
+    int rc = check_modulus_wide(q, width, &Q);
+    if (rc) return rc;
+    if (n == 0) return MQ_OK;
+    if ((rc = check_ptr(c, width, op == OP_AXPY ? "d_y" : "d_c")) || (rc = check_ptr(a, width, op == OP_AXPY ? "d_x" : "d_a")))
+        return rc;
+    if (op != OP_AXPY && (rc = check_ptr(b, width, "d_b"))) return rc;
+    if (n > SIZE_MAX / 32) return mq_fail(MQ_ERR_ARG, "n overflows");
+    BlasWideArgs args;
+    memset(&args, 0, sizeof args);
+    args.c = c;
+    args.a = a;
+    args.b = b;
+    args.n = n;
+    hw::to_words(Q, args.q, width);
+    args.L = hw::bitlen(Q);
+    hw::to_words(hw::barrett_mu(Q, args.L), args.mu, width);
+    if (op == OP_AXPY) {
+        if (!scalar) return mq_fail(MQ_ERR_ARG, "scalar a is NULL");
+        const hw::U sv = hw::from_words(scalar, width);
+        if (hw::cmp(sv, Q) >= 0) return mq_fail(MQ_ERR_RANGE, "scalar a must be < q");
+        hw::to_words(sv, args.s, width);
+        hw::to_words(hw::shoup(sv, Q, 64 * width), args.sp, width);
+    }
+    cudaError_t e = launch_blas_wide(width, op, args, (cudaStream_t)stream);
+    return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "BLAS launch");
+}
+
 static int blas(int op, void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width,
                 const uint64_t *scalar, void *stream) {
+    if (width == MQ_W192 || width == MQ_W256) return blas_wide(op, c, a, b, n, q, width, scalar, stream);
     hm::u128 Q;
     int rc = mq_check_modulus(q, width, &Q);
     if (rc) return rc;

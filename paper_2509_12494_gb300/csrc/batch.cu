@@ -113,6 +113,7 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
     if (is_ntt(j.kind)) {
         const ntt_plan *p = j.plan;
         if (!p) return mq_fail(MQ_ERR_ARG, "job %zu: NTT job without a plan", index);
+        if (p->width > MQ_W128) return mq_fail(MQ_ERR_ARG, "job %zu: the batched form takes residues of one or two words", index);
         if (p->log2n < LMIN || p->log2n > 2 * LMAX)
             return mq_fail(MQ_ERR_SIZE, "job %zu: batched transforms need 2^%d <= N <= 2^%d", index, LMIN, 2 * LMAX);
         if (!j.data) return mq_fail(MQ_ERR_ARG, "job %zu: data is NULL", index);

@@ -29,9 +29,9 @@ struct PassArgs {
     const void *in;      // source residues
     void *out;           // destination residues (may equal in)
     const void *tw;      // twiddle table (N entries, forward or inverse)
-    uint64_t q[2];       // modulus, low word first
-    uint64_t sc[2], scp[2];  // N^-1 and its Shoup companion (inverse, global stage 0)
-    uint64_t ws[2], wsp[2];  // twiddle[1] * N^-1 and its Shoup companion
+    uint64_t q[4];       // modulus, low word first (words beyond the residue width are zero)
+    uint64_t sc[4], scp[4];  // N^-1 and its Shoup companion (inverse, global stage 0)
+    uint64_t ws[4], wsp[4];  // twiddle[1] * N^-1 and its Shoup companion
     size_t in_stride;    // residues between consecutive polynomials in `in`
     size_t out_stride;   // ... in `out`
     unsigned long long batch;  // polynomials
@@ -75,5 +75,16 @@ struct BlasArgs {
     uint64_t s[2], sp[2];  // axpy scalar and its Shoup companion
 };
 cudaError_t launch_blas(int width, int op, const BlasArgs &a, cudaStream_t s);
+
+// The same operations on residues of three and four 64-bit words (see blas_wide.cu).
+struct BlasWideArgs {
+    void *c;
+    const void *a, *b;
+    size_t n;
+    uint64_t q[4], mu[4];
+    int L;
+    uint64_t s[4], sp[4];  // axpy scalar and its Shoup companion
+};
+cudaError_t launch_blas_wide(int width, int op, const BlasWideArgs &a, cudaStream_t s);
 
 }  // namespace mq

@@ -3,9 +3,14 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "wide.cuh"
 
 namespace mq {
 
+cudaError_t launch_ntt_w3_fwd(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w3_inv(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w4_fwd(int L, const PassArgs &a, cudaStream_t s);
+cudaError_t launch_ntt_w4_inv(int L, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_ntt_w1_fwd(int L, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_ntt_w1_inv(int L, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_ntt_w2_fwd(int L, const PassArgs &a, cudaStream_t s);
@@ -97,6 +102,71 @@ __global__ void twiddle_kernel128(int logN, int cyclic, Mod128 m, uint4 root, ui
     }
 }
 
+// residues of three and four words (wide.cuh): the same tables, entries of 2 NL words (w, w')
+template <int NL>
+__device__ Wide<NL> shoup_companion(const Wide<NL> &w, const Wide<NL> &q) {  // floor(w 2^(64 NL) / q), q < 2^(64 NL - 4)
+    Wide<NL> r = w, quo;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) quo.w[k] = 0;
+    for (int i = 0; i < 64 * NL; ++i) {
+        r = add_nored(r, r);
+        quo = add_nored(quo, quo);
+        uint64_t br;
+        const Wide<NL> d = sub_wide(r, q, br);
+        if (!br) {
+            r = d;
+            quo.w[0] |= 1;
+        }
+    }
+    return quo;
+}
+
+template <int NL>
+__device__ Wide<NL> pow_mod(const Wide<NL> &g, unsigned e, const ModW<NL> &m) {
+    Wide<NL> acc;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) acc.w[k] = k == 0;
+    for (int b = 31; b >= 0; --b) {
+        acc = mul_mod_barrett(acc, acc, m);
+        if ((e >> b) & 1) acc = mul_mod_barrett(acc, g, m);
+    }
+    return acc;
+}
+
+template <int NL>
+__global__ void twiddle_kernel_wide(int logN, int cyclic, ModW<NL> m, Wide<NL> root, Wide<NL> root_inv,
+                                    uint64_t *fwd, uint64_t *inv) {
+    unsigned N = 1u << logN;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        unsigned e = table_exponent(k, logN, cyclic);
+        const Wide<NL> w = pow_mod(root, e, m), wi = pow_mod(root_inv, e, m);
+        const Wide<NL> wp = shoup_companion(w, m.q), wip = shoup_companion(wi, m.q);
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+            fwd[2 * NL * (size_t)k + j] = w.w[j];
+            fwd[2 * NL * (size_t)k + NL + j] = wp.w[j];
+            inv[2 * NL * (size_t)k + j] = wi.w[j];
+            inv[2 * NL * (size_t)k + NL + j] = wip.w[j];
+        }
+    }
+}
+
+template <int NL>
+void launch_twiddles_wide(int logN, int cyclic, const uint64_t *q, const uint64_t *root, const uint64_t *root_inv,
+                          const uint64_t *mu, int L, void *tw_fwd, void *tw_inv, unsigned blocks, unsigned threads,
+                          cudaStream_t s) {
+    ModW<NL> m;
+    Wide<NL> r, ri;
+    for (int k = 0; k < NL; ++k) {
+        m.q.w[k] = q[k];
+        m.mu.w[k] = mu[k];
+        r.w[k] = root[k];
+        ri.w[k] = root_inv[k];
+    }
+    m.L = L;
+    twiddle_kernel_wide<NL><<<blocks, threads, 0, s>>>(logN, cyclic, m, r, ri, (uint64_t *)tw_fwd, (uint64_t *)tw_inv);
+}
+
 uint4 to_u4(const uint64_t v[2]) {
     return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1], (uint32_t)(v[1] >> 32));
 }
@@ -105,6 +175,8 @@ uint4 to_u4(const uint64_t v[2]) {
 
 cudaError_t launch_ntt_pass(int width, int L, bool inv, const PassArgs &a, cudaStream_t s) {
     if (width == 1) return inv ? launch_ntt_w1_inv(L, a, s) : launch_ntt_w1_fwd(L, a, s);
+    if (width == 3) return inv ? launch_ntt_w3_inv(L, a, s) : launch_ntt_w3_fwd(L, a, s);
+    if (width == 4) return inv ? launch_ntt_w4_inv(L, a, s) : launch_ntt_w4_fwd(L, a, s);
     return inv ? launch_ntt_w2_inv(L, a, s) : launch_ntt_w2_fwd(L, a, s);
 }
 
@@ -116,6 +188,10 @@ cudaError_t launch_twiddle_build(int width, int logN, int cyclic, const uint64_t
     if (width == 1) {
         Mod64 m{q[0], mu[0], L};
         twiddle_kernel64<<<blocks, threads, 0, s>>>(logN, cyclic, m, root[0], root_inv[0], (Tw64 *)tw_fwd, (Tw64 *)tw_inv);
+    } else if (width == 3) {
+        launch_twiddles_wide<3>(logN, cyclic, q, root, root_inv, mu, L, tw_fwd, tw_inv, blocks, threads, s);
+    } else if (width == 4) {
+        launch_twiddles_wide<4>(logN, cyclic, q, root, root_inv, mu, L, tw_fwd, tw_inv, blocks, threads, s);
     } else {
         Mod128 m{to_u4(q), to_u4(mu), L};
         twiddle_kernel128<<<blocks, threads, 0, s>>>(logN, cyclic, m, to_u4(root), to_u4(root_inv), (Tw128 *)tw_fwd,

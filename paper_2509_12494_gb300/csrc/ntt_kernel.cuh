@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "wide.cuh"
 
 namespace mq {
 namespace ntt_detail {
@@ -58,6 +59,27 @@ struct Traits<2> {
     }
 };
 
+// residues of three and four 64-bit words (wide.cuh); a twiddle entry is (w, w') of 2 NL words
+template <int NL>
+struct TraitsWide {
+    typedef Wide<NL> E;
+    typedef Wide<NL> TW;  // first of the entry's two values; the companion follows it
+    static constexpr int EPR = 4;  // swizzle group (a permutation of each run of 4 residues)
+    __device__ __forceinline__ static E make(const uint64_t *v) { return wide_from<NL>(v); }
+    __device__ __forceinline__ static void load_tw(const TW *t, unsigned idx, E &w, E &wp) {
+        const uint64_t *p = reinterpret_cast<const uint64_t *>(t) + 2 * NL * (size_t)idx;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            w.w[k] = __ldg(reinterpret_cast<const unsigned long long *>(p) + k);
+            wp.w[k] = __ldg(reinterpret_cast<const unsigned long long *>(p) + NL + k);
+        }
+    }
+};
+template <>
+struct Traits<3> : TraitsWide<3> {};
+template <>
+struct Traits<4> : TraitsWide<4> {};
+
 constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 constexpr int maxc(int a, int b) { return a > b ? a : b; }
 
@@ -65,11 +87,12 @@ constexpr int maxc(int a, int b) { return a > b ? a : b; }
 template <int W, int L>
 struct Shape {
     static constexpr int T = 1 << L;                 // residues per tile
-    static constexpr int R = T < 8 ? T : 8;          // residues per thread (radix)
+    static constexpr int RMAX = W <= 2 ? 8 : 4;      // radix: wide residues hold 4 per thread
+    static constexpr int R = T < RMAX ? T : RMAX;    // residues per thread (radix)
     static constexpr int r = ilog2c(R);              // stages per register round
     static constexpr int TPT = T / R;                // threads per tile
-    // tiles per CTA: 256 threads for tiles up to 2^11, 512 for 2^12
-    static constexpr int G = (L <= 11) ? (256 / TPT) : 1;
+    // tiles per CTA: 256 threads for tiles up to 2^11 (up to 2^10 for wide residues), 512 for 2^12
+    static constexpr int G = (TPT <= 256) ? (256 / TPT) : 1;
     static constexpr int NT = G * TPT;               // threads per CTA
     static constexpr int TS = T + 1;                 // padded tile stride in shared memory
     static constexpr int ROUNDS = (L + r - 1) / r;
@@ -365,7 +388,7 @@ __device__ __forceinline__ void tile_group(const PassArgs &a, unsigned long long
 // of gridDim.x and prefetches the next group's tiles (cp.async into the second of two shared
 // buffers) while it transforms the current one.
 template <int W, int L, bool INV>
-__global__ void __launch_bounds__(Shape<W, L>::NT, (Shape<W, L>::NT <= 256) ? 3 : 1)
+__global__ void __launch_bounds__(Shape<W, L>::NT, W > 2 ? 2 : ((Shape<W, L>::NT <= 256) ? 3 : 1))
     ntt_pass_kernel(const PassArgs a, unsigned long long groups) {
     typedef typename Traits<W>::E E;
     typedef Shape<W, L> S;

@@ -7,10 +7,10 @@ struct ntt_plan {
     unsigned log2n;
     int width;
     unsigned flags;
-    uint64_t q[2], mu[2];
+    uint64_t q[4], mu[4];  // low word first; residues of up to four 64-bit words
     int L;  // bit length of q
-    uint64_t root[2], root_inv[2];
+    uint64_t root[4], root_inv[4];
     void *tw_fwd, *tw_inv;  // N entries of (w, w') each
-    uint64_t sc[2], scp[2], ws[2], wsp[2];
+    uint64_t sc[4], scp[4], ws[4], wsp[4];
     int L1;  // rows of the N1 x N2 split (0: single pass)
 };

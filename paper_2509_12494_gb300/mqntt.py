@@ -21,10 +21,11 @@ from . import _build
 MQ_OK = 0
 MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_ALIGN = -1, -2, -3, -4, -5
 MQ_ERR_OOM, MQ_ERR_CUDA, MQ_ERR_TIMEOUT, MQ_ERR_RANGE, MQ_ERR_STATE = -6, -7, -8, -9, -10
-MQ_W64, MQ_W128 = 1, 2
+MQ_W64, MQ_W128, MQ_W192, MQ_W256 = 1, 2, 3, 4
 MQ_NEGACYCLIC, MQ_CYCLIC, MQ_ORDER_NATURAL, MQ_ORDER_BITREV = 0, 1, 0, 2
 
 _u64x2 = ctypes.c_uint64 * 2
+_u64p = ctypes.POINTER(ctypes.c_uint64)
 _vp = ctypes.c_void_p
 _lib = None
 
@@ -52,17 +53,17 @@ def load(build_if_missing: bool = False):
         _build.build()
     L = ctypes.CDLL(path)
     sig = {
-        "ntt_plan_create": [ctypes.POINTER(_vp), ctypes.c_uint, _u64x2, _u64x2, ctypes.c_int, ctypes.c_uint, _vp],
+        "ntt_plan_create": [ctypes.POINTER(_vp), ctypes.c_uint, _u64p, _u64p, ctypes.c_int, ctypes.c_uint, _vp],
         "ntt_plan_destroy": [_vp],
         "ntt_forward": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_inverse": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_polymul": [_vp, _vp, _vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_forward_noalloc": [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp],
         "ntt_plan_info": [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint)],
-        "mod_vadd": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
-        "mod_vsub": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
-        "mod_vmul": [_vp, _vp, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
-        "mod_axpy": [_vp, _u64x2, _vp, ctypes.c_size_t, _u64x2, ctypes.c_int, _vp],
+        "mod_vadd": [_vp, _vp, _vp, ctypes.c_size_t, _u64p, ctypes.c_int, _vp],
+        "mod_vsub": [_vp, _vp, _vp, ctypes.c_size_t, _u64p, ctypes.c_int, _vp],
+        "mod_vmul": [_vp, _vp, _vp, ctypes.c_size_t, _u64p, ctypes.c_int, _vp],
+        "mod_axpy": [_vp, _u64p, _vp, ctypes.c_size_t, _u64p, ctypes.c_int, _vp],
         "mq_probe_imad_rate": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), _vp],
         "mq_probe_mulmod": [ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _u64x2, _vp],
@@ -99,11 +100,13 @@ def load(build_if_missing: bool = False):
 
 # ---------------------------------------------------------------------------------------- helpers
 
-def words(v: int) -> "ctypes.Array":
+def words(v: int, width: int = 2) -> "ctypes.Array":
+    """v as max(width, 2) 64-bit words, low first (the ABI's modulus / root / scalar arrays)."""
     v = int(v)
-    if v < 0 or v >= 2**128:
-        raise ValueError("value must be in [0, 2^128)")
-    return _u64x2(v & (2**64 - 1), v >> 64)
+    n = max(width, 2)
+    if v < 0 or v >= 2 ** (64 * n):
+        raise ValueError(f"value must be in [0, 2^{64 * n})")
+    return (ctypes.c_uint64 * n)(*[(v >> (64 * k)) & (2**64 - 1) for k in range(n)])
 
 
 def ptr(x) -> int:
@@ -130,7 +133,7 @@ def _check(rc: int):
 
 
 def width_of(q: int) -> int:
-    return MQ_W64 if q < 2**60 else MQ_W128
+    return MQ_W64 if q < 2**60 else MQ_W128 if q < 2**124 else MQ_W192 if q < 2**188 else MQ_W256
 
 
 # ---------------------------------------------------------------------------------------- the ABI
@@ -149,7 +152,8 @@ class Plan:
 
 def ntt_plan_create(log2n: int, q: int, root: int, width: int, flags: int = 0, stream=None) -> Plan:
     h = _vp()
-    _check(load().ntt_plan_create(ctypes.byref(h), log2n, words(q), words(root), width, flags, stream_handle(stream)))
+    _check(load().ntt_plan_create(ctypes.byref(h), log2n, words(q, width), words(root, width), width, flags,
+                                  stream_handle(stream)))
     return Plan(h.value, log2n, width, flags)
 
 
@@ -186,19 +190,19 @@ def ntt_plan_info(plan: Plan):
 
 
 def mod_vadd(c, a, b, n: int, q: int, width: int, stream=None):
-    _check(load().mod_vadd(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+    _check(load().mod_vadd(ptr(c), ptr(a), ptr(b), n, words(q, width), width, stream_handle(stream)))
 
 
 def mod_vsub(c, a, b, n: int, q: int, width: int, stream=None):
-    _check(load().mod_vsub(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+    _check(load().mod_vsub(ptr(c), ptr(a), ptr(b), n, words(q, width), width, stream_handle(stream)))
 
 
 def mod_vmul(c, a, b, n: int, q: int, width: int, stream=None):
-    _check(load().mod_vmul(ptr(c), ptr(a), ptr(b), n, words(q), width, stream_handle(stream)))
+    _check(load().mod_vmul(ptr(c), ptr(a), ptr(b), n, words(q, width), width, stream_handle(stream)))
 
 
 def mod_axpy(y, a: int, x, n: int, q: int, width: int, stream=None):
-    _check(load().mod_axpy(ptr(y), words(a), ptr(x), n, words(q), width, stream_handle(stream)))
+    _check(load().mod_axpy(ptr(y), words(a, width), ptr(x), n, words(q, width), width, stream_handle(stream)))
 
 
 MQ_PROBE_MAD_LO, MQ_PROBE_MAD_HI, MQ_PROBE_MAD_CC, MQ_PROBE_MAD_WIDE = 0, 1, 2, 3

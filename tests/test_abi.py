@@ -57,7 +57,7 @@ Q124 = (1 << 123) + (1 << 20) + 1   # not checked for primality: the checks belo
     (dict(q=2**60 + 1, width=M.MQ_W64), M.MQ_ERR_MODULUS),
     (dict(q=(1 << 100)), M.MQ_ERR_MODULUS),            # even
     (dict(q=(3 << 100) + 3), M.MQ_ERR_MODULUS),         # q - 1 not divisible by 2N
-    (dict(width=3), M.MQ_ERR_ARG),
+    (dict(width=5), M.MQ_ERR_ARG),
     (dict(flags=8), M.MQ_ERR_ARG),
     (dict(root=0), M.MQ_ERR_ROOT),
     (dict(root=Q124), M.MQ_ERR_ROOT),                   # root >= q
@@ -97,3 +97,17 @@ def test_polymul_rejects_without_touching_the_device(lib):
     so = M.load()
     assert so.ntt_polymul(None, 16, 16, 16, 1, 0, None) == M.MQ_ERR_ARG
     assert "plan" in M.mq_last_error()
+
+
+def test_wide_plan_rejects_without_touching_the_device(lib):
+    q188 = (1 << 187) + (1 << 20) + 1   # shape checks come before any device call
+    for kw, code in ((dict(q=(1 << 187) + (1 << 20)), M.MQ_ERR_MODULUS),        # even
+                     (dict(q=(1 << 189) + 1), M.MQ_ERR_MODULUS),                  # above 2^188
+                     (dict(q=(1 << 187) + 3), M.MQ_ERR_MODULUS),                  # q - 1 not divisible by 2N
+                     (dict(root=0), M.MQ_ERR_ROOT),
+                     (dict(log2n=21), M.MQ_ERR_SIZE)):
+        args = dict(log2n=10, q=q188, root=5, width=M.MQ_W192, flags=0)
+        args.update(kw)
+        with pytest.raises(M.MqError) as e:
+            M.ntt_plan_create(args["log2n"], args["q"], args["root"], args["width"], args["flags"], stream=0)
+        assert e.value.code == code, (kw, M.mq_last_error())
