@@ -209,7 +209,7 @@ static int check_args(const uint64_t *q, int width) {
     return 0;
 }
 
-/* The widest residue (in 64-bit words) this build takes: 2, or 4 for the wide build. */
+/* The widest residue (in 64-bit words) this compiled copy takes: 2, or 4 for the wide build. */
 int oracle_max_width(void) { return MAX_WIDTH; }
 
 /* ---------------------------------------------------------------- BLAS (Sec. 2.3) */
