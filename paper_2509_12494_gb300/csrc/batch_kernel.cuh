@@ -171,6 +171,7 @@ __device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned
 template <int WM, bool BL>
 struct KCfg {
     static constexpr int MINB = (WM == 1 && !BL) ? 3 : 2;  // resident CTAs per SM the registers allow
+    static constexpr int PMINB = (WM == 1 && !BL) ? 4 : 3; // the same for the prefetching form
     static constexpr int W = (WM & 2) ? 2 : 1;              // widest residue (sizes the tile buffers)
 };
 
@@ -307,7 +308,7 @@ __device__ __forceinline__ void copy_record(ItemDev *dst, const ItemDev *src) {
 // order taken and depend only on items taken before them, so every wait ends (the unfinished
 // item of lowest index always has its dependencies done and its CTA working on it).
 template <int WM, bool BL>
-__global__ void __launch_bounds__(BT, 3)
+__global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     prefetch_kernel(const JobDev *__restrict__ jobs, const ItemDev *__restrict__ items, unsigned n_items,
                     unsigned *ctrs, unsigned njobs, unsigned long long limit_ns, size_t buf_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -447,7 +448,7 @@ inline size_t kernel_smem() {
 template <int FORM, int WM, bool BL>
 struct PersistentKernel {
     static constexpr int THREADS = FORM ? BT : CT;
-    static constexpr int MAXB = FORM ? 3 : KCfg<WM, BL>::MINB;  // CTAs per SM the registers allow
+    static constexpr int MAXB = FORM ? KCfg<WM, BL>::PMINB : KCfg<WM, BL>::MINB;  // CTAs per SM the registers allow
     // set the shared-memory limit; *per_sm = resident CTAs per SM, *smem = bytes of one buffer
     static cudaError_t configure(int *per_sm, size_t *smem);
     static cudaError_t launch(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, unsigned *dctrs,

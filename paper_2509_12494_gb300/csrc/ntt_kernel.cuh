@@ -388,7 +388,7 @@ __device__ __forceinline__ void tile_group(const PassArgs &a, unsigned long long
 // of gridDim.x and prefetches the next group's tiles (cp.async into the second of two shared
 // buffers) while it transforms the current one.
 template <int W, int L, bool INV>
-__global__ void __launch_bounds__(Shape<W, L>::NT, W > 2 ? 2 : ((Shape<W, L>::NT <= 256) ? 3 : 1))
+__global__ void __launch_bounds__(Shape<W, L>::NT, W > 2 ? 2 : ((Shape<W, L>::NT <= 256) ? (W == 1 ? 4 : 3) : 1))
     ntt_pass_kernel(const PassArgs a, unsigned long long groups) {
     typedef typename Traits<W>::E E;
     typedef Shape<W, L> S;

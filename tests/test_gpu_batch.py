@@ -270,16 +270,18 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(mq, form):
 @pytest.mark.parametrize("form", FORMS)
 def test_instantiation_follows_batch_contents(mq, form):
     """Split form: 64-bit transforms alone run three persistent CTAs per SM, any batch with 128-bit
-    residues or BLAS two.  Prefetch form: three for every batch.  An explicit ctas_per_sm is clamped
-    to what the instantiation holds.  Each batch's results equal the per-call path's."""
+    residues or BLAS two.  Prefetch form: four for 64-bit transforms alone, three otherwise.  An
+    explicit ctas_per_sm is clamped to what the instantiation holds.  Each batch's results equal the
+    per-call path's."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     c60 = NttCase(mq, 14, 60, 2, 0, False, 61)
     c124 = NttCase(mq, 14, 124, 2, 0, True, 62)
     bl = BlasCase(mq, "vmul", 70001, 60, 63)
     two = 2 if form == "split" else 3
-    for jobs, ctas, kw in (([c60], 3, {}), ([c124], two, {}), ([c60, c124], two, {}), ([bl], two, {}),
-                           ([c60], 3, {"ctas_per_sm": 7}), ([c124], two, {"ctas_per_sm": 7}),
+    alone60 = 3 if form == "split" else 4
+    for jobs, ctas, kw in (([c60], alone60, {}), ([c124], two, {}), ([c60, c124], two, {}), ([bl], two, {}),
+                           ([c60], alone60, {"ctas_per_sm": 7}), ([c124], two, {"ctas_per_sm": 7}),
                            ([c60], 1, {"ctas_per_sm": 1})):
         wants = [j.per_call() if isinstance(j, NttCase) else None for j in jobs]
         for j in jobs:
