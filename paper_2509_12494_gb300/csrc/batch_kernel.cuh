@@ -297,7 +297,7 @@ __device__ __forceinline__ void copy_record(ItemDev *dst, const ItemDev *src) {
 // The prefetching form: all BT threads compute, and each CTA prefetches its next item while it
 // transforms the current one (the per-call pass kernel's double buffering, with items from the
 // work list).  No warps are set aside for staging, so every thread keeps the register budget of
-// the per-call kernel (three CTAs per SM).
+// the per-call kernel (three CTAs per SM, four for 64-bit transforms alone).
 //
 // Thread 0 runs the item bookkeeping ahead of the transform so that its memory round trips
 // overlap the arithmetic: while item k is transformed it already holds the index of item k + 3
