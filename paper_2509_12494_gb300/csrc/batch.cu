@@ -565,6 +565,11 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             destroy_batch(b);
             return mq_cuda_fail(e, "graph instantiate");
         }
+        // upload now, so that the first launch does not pay for it on the caller's stream
+        if ((e = cudaGraphUpload(b->exec, b->cs)) != cudaSuccess || (e = cudaStreamSynchronize(b->cs)) != cudaSuccess) {
+            destroy_batch(b);
+            return mq_cuda_fail(e, "graph upload");
+        }
     }
     *out = b;
     return MQ_OK;
