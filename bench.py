@@ -37,6 +37,7 @@ HBM_FALLBACK_GBS = 6800.0
 # steps of the pipelined end-to-end job: its fill (the first input copy) and drain (the last result
 # copy) are paid once per job, as in a serving loop that runs continuously
 E2E_STEPS = 32
+E2E_JOBS = 3      # the e2e figure is the median of this many jobs (the host link's rate varies)
 
 
 def parse():
@@ -479,7 +480,7 @@ def run_gpu(args, rank, world):
 
     e2e_run(args.warmup)
     n_e2e = max(E2E_STEPS, args.steps)
-    ms_e2e = e2e_run(n_e2e)
+    ms_e2e = statistics.median(e2e_run(n_e2e) for _ in range(E2E_JOBS))
     exact = all(np.array_equal(h.numpy().view(np.uint64).reshape(x_host.shape), x_host)
                 for h in host_out[:min(nbuf, args.warmup + n_e2e)])
 
@@ -506,22 +507,24 @@ def run_gpu(args, rank, world):
         return t0.elapsed_time(t1) / steps
 
     link_run(1)
-    ms_link = link_run(n_e2e)
+    ms_link = statistics.median(link_run(n_e2e) for _ in range(E2E_JOBS))
 
     t_ser = timed(step_e2e_serial, max(3, args.steps // 2), 1)
     ms_ser = sum(t_ser) / len(t_ser)
     torch.cuda.synchronize()
     out["e2e"] = {"value": bfly / (ms_e2e * 1e-3), "unit": "butterflies/s", "ms_per_step": ms_e2e,
                   "h2d_bytes_per_step": host_in.numel() * 8, "d2h_bytes_per_step": host_out[0].numel() * 8,
-                  "bit_exact": bool(exact), "steps": n_e2e,
+                  "bit_exact": bool(exact), "steps": n_e2e, "jobs": E2E_JOBS,
                   "form": f"pipelined: later steps' input copies and earlier steps' result copies overlap each "
-                          f"step ({nbuf} device buffers, two copy streams); value = steps / total time",
+                          f"step ({nbuf} device buffers, two copy streams); value = steps / total time of a job, "
+                          f"median of {E2E_JOBS} jobs",
                   "link_ms_per_step": ms_link, "link_frac": ms_link / ms_e2e,
                   "serial_ms_per_step": ms_ser, "serial_value": bfly / (ms_ser * 1e-3)}
     del dbuf[1:], pbs[1:]
 
     if not args.no_blas:
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
+        out["small_ntt"] = bench_small_ntt(M, torch, dev, stream)
     if not args.no_uneven:
         out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args))
     if width == 2:   # the two forms of the double-word product (Sec. 2.2, Eq. 8 and 9), multiply-bound
@@ -611,43 +614,103 @@ def bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mad
                          f"x {barrett_mads} (32-bit multiply instructions)"}
 
 
+def time_reps(torch, stream, call, flush=None, reps=20, warm=5):
+    """Median and min event time (ms) of `call` over `reps` timed reps after `warm` untimed ones; the L2
+    flush (if given) runs between reps, outside the events."""
+    times = []
+    with torch.cuda.stream(stream):
+        for i in range(warm + reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            if flush is not None:
+                flush_l2(flush)
+            if i >= warm:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+    ms = [x.elapsed_time(y) for x, y in times]
+    return statistics.median(ms), min(ms)
+
+
 def bench_blas(M, torch, dev, stream, flush):
-    """vadd / vsub / vmul / axpy over n = 2^24 residues, 60- and 124-bit q, L2 flushed between reps."""
+    """vadd / vsub / vmul / axpy, 60- and 124-bit q: n = 2^24 and 2^20 with L2 flushed between reps
+    (2^20 also L2-warm), and the paper's n = 1024 (L2-warm, launch-latency bound)."""
     from paper_2509_12494_gb300 import workload as W
     res = {}
-    n = 1 << 24
     sh = stream.cuda_stream
     hbm_peak = measured_peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
     for bits, width in ((60, 1), (124, 2)):
         q = W.gen_prime(bits, 18, 2)
-        a, b = M.to_device(W.gen_residues(n, q, 1, width), dev), M.to_device(W.gen_residues(n, q, 2, width), dev)
-        c = torch.empty_like(a)
         s = 0x1234567 % q
-        for op in ("vadd", "vsub", "vmul", "axpy"):
-            def call():
-                if op == "axpy":
-                    M.mod_axpy(c, s, a, n, q, width, stream=sh)
+        for log2n in (24, 20, 10):
+            n = 1 << log2n
+            a, b = M.to_device(W.gen_residues(n, q, 1, width), dev), M.to_device(W.gen_residues(n, q, 2, width), dev)
+            c = torch.empty_like(a)
+            for op in ("vadd", "vsub", "vmul", "axpy"):
+                def call():
+                    if op == "axpy":
+                        M.mod_axpy(c, s, a, n, q, width, stream=sh)
+                    else:
+                        getattr(M, "mod_" + op)(c, a, b, n, q, width, stream=sh)
+                nbytes = 3 * n * 8 * width
+                if log2n == 10:
+                    ms, ms_min = time_reps(torch, stream, call)
+                    entry = {"us": ms * 1e3, "us_min": ms_min * 1e3, "elements/s": n / (ms * 1e-3),
+                             "l2": "warm (the 48 KiB working set stays on chip)"}
                 else:
-                    getattr(M, "mod_" + op)(c, a, b, n, q, width, stream=sh)
-            times = []
-            with torch.cuda.stream(stream):
-                for i in range(13):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    call()
-                    e1.record(stream)
-                    flush_l2(flush)
-                    if i >= 3:
-                        times.append((e0, e1))
-                torch.cuda.synchronize()
-            ms = statistics.median([x.elapsed_time(y) for x, y in times])
-            gbs = 3 * n * 8 * width / (ms * 1e-3) / 1e9
-            entry = {"ms": ms, "GB/s": gbs, "hbm_frac": gbs / hbm_peak, "elements/s": n / (ms * 1e-3)}
-            if op in ("vmul", "axpy"):
-                entry["modmul/s"] = n / (ms * 1e-3)
-            res[f"{op}_{bits}"] = entry
-        del a, b, c
+                    ms, ms_min = time_reps(torch, stream, call, flush)
+                    gbs = nbytes / (ms * 1e-3) / 1e9
+                    entry = {"ms": ms, "ms_min": ms_min, "GB/s": gbs, "hbm_frac": gbs / hbm_peak,
+                             "elements/s": n / (ms * 1e-3)}
+                    if log2n == 20:
+                        ms_w, _ = time_reps(torch, stream, call)
+                        entry["ms_l2_warm"] = ms_w
+                        entry["GB/s_l2_warm"] = nbytes / (ms_w * 1e-3) / 1e9
+                if op in ("vmul", "axpy"):
+                    entry["modmul/s"] = entry["elements/s"]
+                res[f"{op}_{bits}" if log2n == 24 else f"{op}_{bits}_n2^{log2n}"] = entry
+            del a, b, c
     return res
+
+
+def bench_small_ntt(M, torch, dev, stream):
+    """One negacyclic forward + inverse transform of N = 1024 under a 124-bit q = 1 mod 2048 (seeds 1..5),
+    as two calls and as a two-job batch replayed from a graph: latency-bound (one CTA), L2-warm."""
+    from paper_2509_12494_gb300 import workload as W
+    sh = stream.cuda_stream
+    log2n, N = 10, 1024
+    bfly = 2 * (N // 2) * log2n
+    per_seed = []
+    exact = True
+    for seed in range(1, 6):
+        q = W.gen_prime(124, log2n + 1, seed)
+        psi = W.gen_root(q, log2n, seed)
+        plan = M.ntt_plan_create(log2n, q, psi, 2, 0, stream=sh)
+        x = W.gen_residues(N, q, seed, 2)
+        d = M.to_device(x, dev)
+
+        def calls():
+            M.ntt_forward(plan, d, 1, N, stream=sh)
+            M.ntt_inverse(plan, d, 1, N, stream=sh)
+        jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d, 1, N), M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d, 1, N, after=0)]
+        pb = M.mq_batch_create(jobs, None, stream=sh)
+
+        def graph():
+            M.mq_batch_launch(pb, stream=sh)
+        ms_c, min_c = time_reps(torch, stream, calls)
+        ms_g, min_g = time_reps(torch, stream, graph)
+        exact = exact and bool(np.array_equal(M.to_host(d), x)) and M.mq_batch_status(pb) == 0
+        per_seed.append((ms_c, min_c, ms_g, min_g))
+        del pb
+    med = lambda k: statistics.median(r[k] for r in per_seed)
+    return {"workload": "1 x N=1024 negacyclic forward+inverse, 124-bit q = 1 mod 2048, seeds 1..5, "
+                        "median over seeds of the median of 20 reps",
+            "butterflies": bfly, "roundtrip_bit_exact": exact,
+            "calls_us": med(0) * 1e3, "calls_us_min": min(r[1] for r in per_seed) * 1e3,
+            "calls_butterflies/s": bfly / (med(0) * 1e-3),
+            "graph_us": med(2) * 1e3, "graph_us_min": min(r[3] for r in per_seed) * 1e3,
+            "graph_butterflies/s": bfly / (med(2) * 1e-3)}
 
 
 # ----------------------------------------------------------------------------------- uneven batch

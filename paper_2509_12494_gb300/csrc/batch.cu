@@ -48,10 +48,6 @@ int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv);
 namespace mq {
 namespace batch_detail {
 
-
-// tiles of 2^L residues per CTA of 256 threads (the Shape rule for L <= 11)
-inline unsigned tiles_per_cta(int L) { return 1u << (11 - L); }
-
 }  // namespace batch_detail
 }  // namespace mq
 

@@ -11,6 +11,10 @@
 namespace mq {
 namespace batch_detail {
 
+// Transform tiles of 2^L residues per work item (one CTA of 256 threads, 2048 residues), L = 6..11.
+// The kernels' tile shape must agree: batch_kernel.cuh checks it at compile time.
+constexpr unsigned tiles_per_cta(int L) { return 1u << (11 - L); }
+
 constexpr int JK_NTT = 0, JK_BLAS = 1;
 
 struct JobDev {

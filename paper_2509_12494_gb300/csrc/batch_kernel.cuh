@@ -430,6 +430,19 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// The host expands transform passes into items of tiles_per_cta(L) tiles: the tile shape the kernels
+// use must hold exactly that many tiles on the 256 threads of a CTA.
+template <int W, int L>
+constexpr bool group_matches_items() {
+    return Shape<W, L>::G == tiles_per_cta(L) && Shape<W, L>::NT == 256;
+}
+static_assert(group_matches_items<1, 6>() && group_matches_items<1, 7>() && group_matches_items<1, 8>() &&
+                  group_matches_items<1, 9>() && group_matches_items<1, 10>() && group_matches_items<1, 11>(),
+              "64-bit tile groups differ from the host's work items");
+static_assert(group_matches_items<2, 6>() && group_matches_items<2, 7>() && group_matches_items<2, 8>() &&
+                  group_matches_items<2, 9>() && group_matches_items<2, 10>() && group_matches_items<2, 11>(),
+              "128-bit tile groups differ from the host's work items");
+
 // Shared memory of one buffer: the largest tile group of width W (every group holds 2048 residues).
 template <int W>
 inline size_t kernel_smem() {
