@@ -283,12 +283,18 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
 #pragma unroll
         for (int e = 0; e < (1 << RR); ++e) tile[swz<W>(base[k] | (e << b_lo))] = x[k * (1 << RR) + e];
     }
-    tile_sync<BAR, S::NT>();
+    // A tile's TPT threads are consecutive: when they fit in one warp the next round reads only
+    // what this warp wrote, and a warp barrier (which orders shared memory among its threads)
+    // suffices; the warps of a CTA then drift apart between rounds instead of waiting for each other.
+    if (S::TPT <= 32)
+        __syncwarp();
+    else
+        tile_sync<BAR, S::NT>();
 }
 
 // The register rounds of one pass on the CTA's staged tiles: every full round (three stages) runs
 // the same code in a loop; a shorter round, when L is not a multiple of 3, has its own (forward:
-// last, inverse: first).  Called by NT = Shape::NT threads; ends with a barrier.
+// last, inverse: first).  Called by NT = Shape::NT threads; ends with a barrier of the NT threads.
 template <int W, int L, bool INV, int BAR = 0>
 __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long long first_tile,
                                             typename Traits<W>::E *sm, int tid) {
@@ -319,6 +325,7 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
 #pragma unroll 1
         for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
     }
+    if (S::TPT <= 32) tile_sync<BAR, S::NT>();  // what follows reads across tiles
 }
 
 // One CTA's share of a pass on tiles already staged in `sm` (by load_tiles_*): tiles
