@@ -43,6 +43,11 @@ struct Traits<1> {
         w = v.x;
         wp = v.y;
     }
+    __device__ __forceinline__ static void load_tw_shared(const TW *t, unsigned idx, E &w, E &wp) {
+        ulonglong2 v = reinterpret_cast<const ulonglong2 *>(t)[idx];
+        w = v.x;
+        wp = v.y;
+    }
 };
 template <>
 struct Traits<2> {
@@ -56,6 +61,11 @@ struct Traits<2> {
         const uint4 *p = reinterpret_cast<const uint4 *>(t) + 2 * (size_t)idx;
         w = __ldg(p);
         wp = __ldg(p + 1);
+    }
+    __device__ __forceinline__ static void load_tw_shared(const TW *t, unsigned idx, E &w, E &wp) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(t) + 2 * idx;
+        w = p[0];
+        wp = p[1];
     }
 };
 
@@ -83,20 +93,25 @@ struct Traits<4> : TraitsWide<4> {};
 constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 constexpr int maxc(int a, int b) { return a > b ? a : b; }
 
-// Static shape of the kernel for tiles of 2^L residues.
-template <int W, int L>
+// Static shape of the kernel for tiles of 2^L residues.  RL = 0: the throughput shape (8 residues per
+// thread, 4 for wide residues, several tiles per CTA of 256 threads).  RL > 0: the latency shape of
+// launches with too few tiles to fill the GPU: RL residues per thread and one tile per CTA, so that
+// a tile's butterflies spread over more warps and its CTAs over more SMs.
+template <int W, int L, int RL = 0>
 struct Shape {
     static constexpr int T = 1 << L;                 // residues per tile
-    static constexpr int RMAX = W <= 2 ? 8 : 4;      // radix: wide residues hold 4 per thread
+    static constexpr int RMAX = RL ? RL : (W <= 2 ? 8 : 4);  // radix: wide residues hold 4 per thread
     static constexpr int R = T < RMAX ? T : RMAX;    // residues per thread (radix)
     static constexpr int r = ilog2c(R);              // stages per register round
     static constexpr int TPT = T / R;                // threads per tile
     // tiles per CTA: 256 threads for tiles up to 2^11 (up to 2^10 for wide residues), 512 for 2^12
-    static constexpr int G = (TPT <= 256) ? (256 / TPT) : 1;
+    static constexpr int G = RL ? 1 : ((TPT <= 256) ? (256 / TPT) : 1);
     static constexpr int NT = G * TPT;               // threads per CTA
     static constexpr int TS = T + 1;                 // padded tile stride in shared memory
     static constexpr int ROUNDS = (L + r - 1) / r;
     static constexpr size_t SMEM = (size_t)G * TS * sizeof(typename Traits<W>::E);
+    // the latency shape stages its tile's T - 1 twiddles in shared memory (entry 2^s + i: stage s)
+    static constexpr size_t TWSMEM = RL ? (size_t)T * sizeof(typename Traits<W>::TW) : 0;
 };
 
 __device__ __forceinline__ unsigned brv(unsigned v, int bits) { return bits ? (__brev(v) >> (32 - bits)) : 0u; }
@@ -148,11 +163,11 @@ struct TileAddr {
 };
 
 // Stage tiles first_tile .. first_tile + G - 1 into `sm` with ordinary loads through L2.
-template <int W, int L, int NTH = Shape<W, L>::NT>
+template <int W, int L, int NTH = Shape<W, L>::NT, int RL = 0>
 __device__ __forceinline__ void load_tiles_sync(const PassArgs &a, unsigned long long first_tile,
                                                 typename Traits<W>::E *sm, int tid) {
     typedef typename Traits<W>::E E;
-    typedef Shape<W, L> S;
+    typedef Shape<W, L, RL> S;
     const TileAddr ta(a);
     const E *in = reinterpret_cast<const E *>(a.in);
     const bool gfast = a.in_layout != LAYOUT_ROW;
@@ -197,11 +212,11 @@ __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_
 // The same staging with asynchronous copies (cp.async): the caller commits the group and waits
 // for it before the tiles are used.  Tiles past the last polynomial are left unfilled (their
 // results are never stored).
-template <int W, int L, int NTH = Shape<W, L>::NT>
+template <int W, int L, int NTH = Shape<W, L>::NT, int RL = 0>
 __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned long long first_tile,
                                                  typename Traits<W>::E *sm, int tid) {
     typedef typename Traits<W>::E E;
-    typedef Shape<W, L> S;
+    typedef Shape<W, L, RL> S;
     const TileAddr ta(a);
     const E *in = reinterpret_cast<const E *>(a.in);
     const bool gfast = a.in_layout != LAYOUT_ROW;
@@ -216,17 +231,43 @@ __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned lon
     }
 }
 
+// Twiddle base of a tile: stage s of the tile uses entries (base << s) + i, i < 2^s, of the
+// direction's table (column pass: 1; row pass: 2^L1 + the tile's row in bit-reversed order).
+__device__ __forceinline__ unsigned tile_tw_base(const PassArgs &a, unsigned long long tile) {
+    const TileAddr ta(a);
+    const unsigned ti = (unsigned)(tile & ta.mask);
+    return a.col ? 1u : ((1u << a.L1) + (a.perm ? brv(ti, a.L1) : ti));
+}
+
+// Copy the T - 1 twiddles of one tile (cp.async) into `dst`, entry (base << s) + i to 2^s + i, so
+// that the rounds read them from shared memory with base 1.  Entries are 16 (64-bit) or 32 bytes.
+template <int W, int L>
+__device__ __forceinline__ void stage_twiddles_async(const PassArgs &a, unsigned long long tile,
+                                                     typename Traits<W>::TW *dst, int tid, int nth) {
+    typedef typename Traits<W>::TW TW;
+    constexpr int CH = sizeof(TW) / 16;  // 16-byte chunks per entry
+    const unsigned base = tile_tw_base(a, tile);
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.tw);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    for (int c = tid; c < ((1 << L) - 1) * CH; c += nth) {
+        const unsigned k = 1u + (unsigned)(c / CH);  // local entry 1 .. T - 1
+        const int s = 31 - __clz(k);
+        const unsigned gidx = (base << s) + (k - (1u << s));
+        cp_async(d + k * CH + c % CH, src + (size_t)gidx * CH + c % CH);
+    }
+}
+
 // One register round: stages s_begin .. s_begin + RR - 1 of a tile of 2^L residues, each thread
 // holding R residues (R / 2^RR independent groups of 2^RR), read from and written back to the
 // shared-memory tile, then a barrier.  s_begin is a runtime value so that all full rounds share
 // this code (the instruction footprint matters when several kernels' tiles share one SM).
-template <int W, int L, int RR, bool INV, int BAR = 0>
+template <int W, int L, int RR, bool INV, int BAR = 0, int RL = 0>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
                                             int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
                                             typename Traits<W>::E q8, typename Traits<W>::E nq) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
-    typedef Shape<W, L> S;
+    typedef Shape<W, L, RL> S;
     constexpr int V = S::R >> RR;  // independent groups per thread
     const int b_lo = L - s_begin - RR, b_hi = L - 1 - s_begin;
     E x[S::R];
@@ -259,7 +300,8 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                 E &v = x[k * (1 << RR) + e0 + half];
                 E w, wp;
                 if (!INV) {
-                    Tr::load_tw(tw, idx, w, wp);
+                    if constexpr (RL > 0) Tr::load_tw_shared(tw, idx, w, wp);
+                    else Tr::load_tw(tw, idx, w, wp);
                     E uu = csub(u, q8);                              // [0, 8q)
                     E tv = mul_mod_shoup_lazy(v, w, wp, q, nq);      // [0, 6q)
                     u = add_nored(uu, tv);                           // [0, 14q)
@@ -270,7 +312,8 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
                     u = mul_mod_shoup_lazy(sum, Tr::make(a.sc), Tr::make(a.scp), q, nq);
                     v = mul_mod_shoup_lazy(dif, Tr::make(a.ws), Tr::make(a.wsp), q, nq);
                 } else {
-                    Tr::load_tw(tw, idx, w, wp);
+                    if constexpr (RL > 0) Tr::load_tw_shared(tw, idx, w, wp);
+                    else Tr::load_tw(tw, idx, w, wp);
                     E dif = add_sub(u, q8, v);                       // (0, 16q)
                     u = csub(add_nored(u, v), q8);                   // [0, 8q)
                     v = mul_mod_shoup_lazy(dif, w, wp, q, nq);       // [0, 6q)
@@ -295,35 +338,31 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
 // The register rounds of one pass on the CTA's staged tiles: every full round (three stages) runs
 // the same code in a loop; a shorter round, when L is not a multiple of 3, has its own (forward:
 // last, inverse: first).  Called by NT = Shape::NT threads; ends with a barrier of the NT threads.
-template <int W, int L, bool INV, int BAR = 0>
+template <int W, int L, bool INV, int BAR = 0, int RL = 0>
 __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long long first_tile,
-                                            typename Traits<W>::E *sm, int tid) {
+                                            typename Traits<W>::E *sm, int tid,
+                                            const typename Traits<W>::TW *tw_sm = nullptr) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
-    typedef Shape<W, L> S;
+    typedef Shape<W, L, RL> S;
     const E q = Tr::make(a.q);
     const E q2 = add_nored(q, q), q4 = add_nored(q2, q2);
     const E q8 = add_nored(q4, q4);
     const E nq = neg(q);
-    const typename Tr::TW *tw = reinterpret_cast<const typename Tr::TW *>(a.tw);
     const int g = tid / S::TPT, t = tid % S::TPT;
-    unsigned tw_base;
-    {
-        const TileAddr ta(a);
-        unsigned long long gt = first_tile + g;
-        unsigned ti = (unsigned)(gt & ta.mask);
-        tw_base = a.col ? 1u : ((1u << a.L1) + (a.perm ? brv(ti, a.L1) : ti));
-    }
+    // the latency shape reads its tile's twiddles from the shared-memory copy, whose base is 1
+    const typename Tr::TW *tw = RL ? tw_sm : reinterpret_cast<const typename Tr::TW *>(a.tw);
+    const unsigned tw_base = RL ? 1u : tile_tw_base(a, first_tile + g);
     E *tile = sm + g * S::TS;
     constexpr int FULL = L / S::r, PART = L - FULL * S::r;
     if (!INV) {
 #pragma unroll 1
-        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
-        if (PART) radix_round<W, L, PART, false, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
+        for (int rho = 0; rho < FULL; ++rho) radix_round<W, L, S::r, false, BAR, RL>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
+        if (PART) radix_round<W, L, PART, false, BAR, RL>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
     } else {
-        if (PART) radix_round<W, L, PART, true, BAR>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
+        if (PART) radix_round<W, L, PART, true, BAR, RL>(a, tile, t, tw_base, FULL * S::r, tw, q, q8, nq);
 #pragma unroll 1
-        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
+        for (int rho = FULL - 1; rho >= 0; --rho) radix_round<W, L, S::r, true, BAR, RL>(a, tile, t, tw_base, rho * S::r, tw, q, q8, nq);
     }
     if (S::TPT <= 32) tile_sync<BAR, S::NT>();  // what follows reads across tiles
 }
@@ -341,12 +380,13 @@ __device__ __forceinline__ void tile_rounds(const PassArgs &a, unsigned long lon
 //   inverse (GS):  (u, v) <- ((u + v) mod 8q, (u + 8q - v) w mod q + {0, .., 5q})
 // Global loads and stores go through L2 only (.cg), so a pass may read what another SM wrote
 // earlier in the same kernel once the writer's completion is observed.
-template <int W, int L, bool INV, int BAR = 0>
+template <int W, int L, bool INV, int BAR = 0, int RL = 0>
 __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned long long first_tile,
-                                           typename Traits<W>::E *sm, int tid) {
+                                           typename Traits<W>::E *sm, int tid,
+                                           const typename Traits<W>::TW *tw_sm = nullptr) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
-    typedef Shape<W, L> S;
+    typedef Shape<W, L, RL> S;
 
     const E q = Tr::make(a.q);
     const E q2 = add_nored(q, q);
@@ -359,7 +399,7 @@ __device__ __forceinline__ void tile_compute_store(const PassArgs &a, unsigned l
     E *out = reinterpret_cast<E *>(a.out);
     const bool gfast_out = a.out_layout != LAYOUT_ROW;
 
-    tile_rounds<W, L, INV, BAR>(a, first_tile, sm, tid);
+    tile_rounds<W, L, INV, BAR, RL>(a, first_tile, sm, tid, tw_sm);
 
     // ---- shared -> global (canonical residues from the last pass)
     for (int i = tid; i < S::G * S::T; i += S::NT) {
@@ -393,74 +433,116 @@ __device__ __forceinline__ void tile_group(const PassArgs &a, unsigned long long
 
 // A pass over `groups` CTA groups by a persistent grid: each CTA walks the groups with a stride
 // of gridDim.x and prefetches the next group's tiles (cp.async into the second of two shared
-// buffers) while it transforms the current one.
-template <int W, int L, bool INV>
-__global__ void __launch_bounds__(Shape<W, L>::NT, W > 2 ? 2 : ((Shape<W, L>::NT <= 256) ? (W == 1 ? 4 : 3) : 1))
+// buffers) while it transforms the current one.  RL > 0 selects the latency shape (one tile per
+// CTA), whose registers are capped so that 1024 threads fit an SM.
+template <int W, int L, int RL>
+constexpr int pass_min_blocks() {
+    return RL ? (1024 / Shape<W, L, RL>::NT < 32 ? 1024 / Shape<W, L, RL>::NT : 32)
+              : (W > 2 ? 2 : ((Shape<W, L>::NT <= 256) ? (W == 1 ? 4 : 3) : 1));
+}
+
+template <int W, int L, bool INV, int RL = 0>
+__global__ void __launch_bounds__(Shape<W, L, RL>::NT, (pass_min_blocks<W, L, RL>()))
     ntt_pass_kernel(const PassArgs a, unsigned long long groups) {
     typedef typename Traits<W>::E E;
-    typedef Shape<W, L> S;
+    typedef typename Traits<W>::TW TW;
+    typedef Shape<W, L, RL> S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    E *buf0 = reinterpret_cast<E *>(smem_raw), *buf1 = buf0 + S::G * S::TS;
+    // [twiddles 0][twiddles 1] (latency shape only; 16-byte entries or pairs) [tiles 0][tiles 1]
+    TW *tws0 = reinterpret_cast<TW *>(smem_raw), *tws1 = tws0 + (RL ? S::T : 0);
+    E *buf0 = reinterpret_cast<E *>(smem_raw + 2 * S::TWSMEM), *buf1 = buf0 + S::G * S::TS;
     const int tid = threadIdx.x;
     unsigned long long grp = blockIdx.x;
-    if (grp < groups) load_tiles_async<W, L>(a, grp * S::G, buf0, tid);
+    if (grp < groups) {
+        load_tiles_async<W, L, S::NT, RL>(a, grp * S::G, buf0, tid);
+        if constexpr (RL > 0) stage_twiddles_async<W, L>(a, grp, tws0, tid, S::NT);
+    }
     cp_async_commit();
     bool odd = false;
     for (; grp < groups; grp += gridDim.x) {
         E *cur = odd ? buf1 : buf0, *nxt = odd ? buf0 : buf1;
+        TW *twc = odd ? tws1 : tws0, *twn = odd ? tws0 : tws1;
         const unsigned long long next = grp + gridDim.x;
-        if (next < groups) load_tiles_async<W, L>(a, next * S::G, nxt, tid);
+        if (next < groups) {
+            load_tiles_async<W, L, S::NT, RL>(a, next * S::G, nxt, tid);
+            if constexpr (RL > 0) stage_twiddles_async<W, L>(a, next, twn, tid, S::NT);
+        }
         cp_async_commit();
         cp_async_wait_1();  // this thread's copies of the current group have landed
         __syncthreads();    // and everyone else's
-        tile_compute_store<W, L, INV>(a, grp * S::G, cur, tid);
+        tile_compute_store<W, L, INV, 0, RL>(a, grp * S::G, cur, tid, twc);
         odd = !odd;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-template <int W, int L, bool INV>
-cudaError_t launch_one(const PassArgs &a, cudaStream_t s) {
-    typedef Shape<W, L> S;
-    static int per_sm = 0;  // benign race: every thread computes the same values
-    const size_t smem = 2 * S::SMEM;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<W, L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ntt_pass_kernel<W, L, INV>, S::NT, smem);
-        if (e != cudaSuccess) return e;
-        per_sm = n > 0 ? n : 1;
-    }
-    const unsigned long long TP = a.col ? (1ull << (a.logN - a.L1)) : (1ull << a.L1);
-    const unsigned long long tiles = TP * a.batch;
-    const unsigned long long groups = (tiles + S::G - 1) / S::G;
-    if (groups == 0) return cudaSuccess;
+__host__ __forceinline__ int sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned long long wave = (unsigned long long)sms * per_sm;
+    return sms;
+}
+
+__host__ __forceinline__ unsigned long long pass_tiles(const PassArgs &a) {
+    const unsigned long long TP = a.col ? (1ull << (a.logN - a.L1)) : (1ull << a.L1);
+    return TP * a.batch;
+}
+
+template <int W, int L, bool INV, int RL = 0>
+cudaError_t launch_one(const PassArgs &a, cudaStream_t s) {
+    typedef Shape<W, L, RL> S;
+    static int per_sm = 0;  // benign race: every thread computes the same values
+    const size_t smem = 2 * S::SMEM + 2 * S::TWSMEM;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(ntt_pass_kernel<W, L, INV, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ntt_pass_kernel<W, L, INV, RL>, S::NT, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = n > 0 ? n : 1;
+    }
+    const unsigned long long groups = (pass_tiles(a) + S::G - 1) / S::G;
+    if (groups == 0) return cudaSuccess;
+    const unsigned long long wave = (unsigned long long)sm_count() * per_sm;
     const unsigned grid = (unsigned)(groups < wave ? groups : wave);
-    ntt_pass_kernel<W, L, INV><<<grid, S::NT, smem, s>>>(a, groups);
+    ntt_pass_kernel<W, L, INV, RL><<<grid, S::NT, smem, s>>>(a, groups);
     return cudaGetLastError();
+}
+
+// Residues per thread of the latency shape: radix-4 rounds.  Measured on a single transform of
+// 2^10 (124-bit, forward + inverse): 13.6 us with radix-2 rounds, 12.1 with radix-4, 16.1 with
+// radix-8 (fewer warps per tile).
+constexpr int LATENCY_RADIX = 4;
+
+// One pass: the throughput shape, or the latency shape (radix-4 rounds, one tile of 2^L residues on
+// 2^(L-2) threads, its twiddles staged in shared memory) when the throughput shape's CTAs would
+// not give every SM one (a single polynomial or a small batch), for one- and two-word residues
+// and tiles of 2^5 to 2^10 (larger tiles already take a CTA each in the throughput shape).
+template <int W, int L, bool INV>
+cudaError_t launch_pass(const PassArgs &a, cudaStream_t s) {
+    if constexpr (W <= 2 && L >= 5 && L <= 10) {
+        const unsigned long long groups = (pass_tiles(a) + Shape<W, L>::G - 1) / Shape<W, L>::G;
+        if (groups < (unsigned long long)sm_count()) return launch_one<W, L, INV, LATENCY_RADIX>(a, s);
+    }
+    return launch_one<W, L, INV>(a, s);
 }
 
 template <int W, bool INV>
 cudaError_t launch_w(int L, const PassArgs &a, cudaStream_t s) {
     switch (L) {
-    case 1: return launch_one<W, 1, INV>(a, s);
-    case 2: return launch_one<W, 2, INV>(a, s);
-    case 3: return launch_one<W, 3, INV>(a, s);
-    case 4: return launch_one<W, 4, INV>(a, s);
-    case 5: return launch_one<W, 5, INV>(a, s);
-    case 6: return launch_one<W, 6, INV>(a, s);
-    case 7: return launch_one<W, 7, INV>(a, s);
-    case 8: return launch_one<W, 8, INV>(a, s);
-    case 9: return launch_one<W, 9, INV>(a, s);
-    case 10: return launch_one<W, 10, INV>(a, s);
-    case 11: return launch_one<W, 11, INV>(a, s);
-    case 12: return launch_one<W, 12, INV>(a, s);
+    case 1: return launch_pass<W, 1, INV>(a, s);
+    case 2: return launch_pass<W, 2, INV>(a, s);
+    case 3: return launch_pass<W, 3, INV>(a, s);
+    case 4: return launch_pass<W, 4, INV>(a, s);
+    case 5: return launch_pass<W, 5, INV>(a, s);
+    case 6: return launch_pass<W, 6, INV>(a, s);
+    case 7: return launch_pass<W, 7, INV>(a, s);
+    case 8: return launch_pass<W, 8, INV>(a, s);
+    case 9: return launch_pass<W, 9, INV>(a, s);
+    case 10: return launch_pass<W, 10, INV>(a, s);
+    case 11: return launch_pass<W, 11, INV>(a, s);
+    case 12: return launch_pass<W, 12, INV>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -127,3 +127,31 @@ def test_uniform_batch_256x65536(mq, pool):
         mq.ntt_inverse(plan, d, batch, N)
         torch.cuda.synchronize()
         assert np.array_equal(mq.to_host(d), x)
+
+
+@pytest.mark.parametrize("flag", ["nega_nat", "nega_brv"])
+@pytest.mark.parametrize("width", [1, 2])
+@pytest.mark.parametrize("log2n", [5, 8, 10, 13, 16])
+def test_ntt_latency_and_throughput_shapes(mq, pool, log2n, width, flag):
+    """A pass with fewer tile groups than SMs runs on the latency shape (one tile per CTA, radix-4
+    rounds, twiddles staged in shared memory), a larger one on the throughput shape: a batch large
+    enough for the second, each sampled polynomial also transformed alone (the first), both equal to
+    the oracle; the batch's inverse brings every polynomial back."""
+    q = Q60 if width == 1 else Q124
+    flags = FLAGS[flag]
+    root = W.gen_root(q, log2n, seed=log2n + 40)
+    N = 1 << log2n
+    batch = 152 * 2048 // N + 1 if N < 152 * 2048 else 1   # every pass: at least 152 groups of 2048 residues
+    x = W.gen_residues(batch * N, q, seed=log2n * 13 + width, width=width)
+    xs = _strided(x, batch, N, N, width)
+    plan = mq.ntt_plan_create(log2n, q, root, width, flags)
+    y = _strided(_gpu_transform(mq, plan, x, batch, N, False), batch, N, N, width)
+    picks = sample_idx(batch, 3, log2n)
+    fut = {int(b): pool.submit(oracle.ntt, xs[b].copy(), log2n, q, root, width, _ofl(flags)) for b in picks}
+    for b in picks:
+        alone = _gpu_transform(mq, plan, xs[b].copy(), 1, N, False)
+        assert np.array_equal(alone, y[b]), f"polynomial {b}: alone and in the batch differ"
+        assert np.array_equal(y[b], fut[int(b)].result()), f"polynomial {b}: differs from the oracle"
+        assert np.array_equal(_gpu_transform(mq, plan, y[b].copy(), 1, N, True), xs[b]), f"polynomial {b}: inverse alone"
+    back = _gpu_transform(mq, plan, y.reshape(x.shape).copy(), batch, N, True)
+    assert np.array_equal(back, x), "inverse of the batch"
