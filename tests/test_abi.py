@@ -87,6 +87,17 @@ def test_blas_rejects(lib, fn):
     f(None, None, None, 0, Q124, M.MQ_W128, stream=0)  # n == 0 is a no-op, pointers unused
 
 
+@pytest.mark.parametrize("width", [1, 2, 3, 4])
+def test_empty_blas_is_a_no_op_at_every_width(lib, width):
+    q = {1: (1 << 59) + 1, 2: Q124, 3: (1 << 187) + (1 << 20) + 1, 4: (1 << 251) + (1 << 20) + 1}[width]
+    for fn in ("mod_vadd", "mod_vsub", "mod_vmul"):
+        getattr(M, fn)(None, None, None, 0, q, width, stream=0)   # n == 0: pointers unused, no launch
+    M.mod_axpy(None, 1, None, 0, q, width, stream=0)
+    with pytest.raises(M.MqError) as e:                            # the modulus is still checked
+        M.mod_vadd(None, None, None, 0, q + 1, width, stream=0)
+    assert e.value.code == M.MQ_ERR_MODULUS
+
+
 def test_axpy_scalar_range(lib):
     with pytest.raises(M.MqError) as e:
         M.mod_axpy(16, Q124, 16, 4, Q124, M.MQ_W128, stream=0)

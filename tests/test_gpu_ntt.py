@@ -155,3 +155,19 @@ def test_ntt_latency_and_throughput_shapes(mq, pool, log2n, width, flag):
         assert np.array_equal(_gpu_transform(mq, plan, y[b].copy(), 1, N, True), xs[b]), f"polynomial {b}: inverse alone"
     back = _gpu_transform(mq, plan, y.reshape(x.shape).copy(), batch, N, True)
     assert np.array_equal(back, x), "inverse of the batch"
+
+
+@pytest.mark.parametrize("width", [1, 2])
+def test_empty_batch_is_a_no_op(mq, width):
+    """batch = 0: transforms and products return at once and leave every buffer as it was."""
+    import torch
+    q = Q60 if width == 1 else Q124
+    log2n, N = 12, 1 << 12
+    plan = mq.ntt_plan_create(log2n, q, W.gen_root(q, log2n, seed=3), width, FLAGS["nega_brv"])
+    x = W.gen_residues(N, q, seed=5, width=width)
+    d, c = mq.to_device(x), mq.to_device(x)
+    mq.ntt_forward(plan, d, 0, N)
+    mq.ntt_inverse(plan, d, 0, N)
+    mq.ntt_polymul(plan, c, d, d, 0, N)
+    torch.cuda.synchronize()
+    assert np.array_equal(mq.to_host(d), x) and np.array_equal(mq.to_host(c), x)
