@@ -232,7 +232,8 @@ __device__ __forceinline__ void load_tiles_async(const PassArgs &a, unsigned lon
 }
 
 // Twiddle base of a tile: stage s of the tile uses entries (base << s) + i, i < 2^s, of the
-// direction's table (column pass: 1; row pass: 2^L1 + the tile's row in bit-reversed order).
+// direction's table (column pass: 1; row pass: 2^L1 + the tile's row, bit-reversed when the pass
+// permutes its rows).
 __device__ __forceinline__ unsigned tile_tw_base(const PassArgs &a, unsigned long long tile) {
     const TileAddr ta(a);
     const unsigned ti = (unsigned)(tile & ta.mask);
@@ -259,7 +260,7 @@ __device__ __forceinline__ void stage_twiddles_async(const PassArgs &a, unsigned
 
 // One register round: stages s_begin .. s_begin + RR - 1 of a tile of 2^L residues, each thread
 // holding R residues (R / 2^RR independent groups of 2^RR), read from and written back to the
-// shared-memory tile, then a barrier.  s_begin is a runtime value so that all full rounds share
+// shared-memory tile, then a barrier (of the warp when one warp holds the tile).  s_begin is a runtime value so that all full rounds share
 // this code (the instruction footprint matters when several kernels' tiles share one SM).
 template <int W, int L, int RR, bool INV, int BAR = 0, int RL = 0>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
