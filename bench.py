@@ -633,6 +633,19 @@ def time_reps(torch, stream, call, flush=None, reps=20, warm=5):
     return statistics.median(ms), min(ms)
 
 
+def back_to_back(torch, stream, call, k=20):
+    """Mean event time (ms) of `call` over k calls queued back to back on `stream` after one warm-up."""
+    with torch.cuda.stream(stream):
+        call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
 def bench_blas(M, torch, dev, stream, flush):
     """vadd / vsub / vmul / axpy, 60- and 124-bit q: n = 2^24 and 2^20 with L2 flushed between reps
     (2^20 also L2-warm), and the paper's n = 1024 (L2-warm, launch-latency bound)."""
@@ -667,6 +680,13 @@ def bench_blas(M, torch, dev, stream, flush):
                         ms_w, _ = time_reps(torch, stream, call)
                         entry["ms_l2_warm"] = ms_w
                         entry["GB/s_l2_warm"] = nbytes / (ms_w * 1e-3) / 1e9
+                        # device time without the host's call latency: 20 launches back to back between
+                        # two events (each followed by the L2 flush, whose own time is subtracted)
+                        ms_fl = back_to_back(torch, stream, lambda: flush_l2(flush))
+                        ms_d = back_to_back(torch, stream, lambda: (call(), flush_l2(flush))) - ms_fl
+                        entry["ms_device"] = ms_d
+                        entry["GB/s_device"] = nbytes / (ms_d * 1e-3) / 1e9
+                        entry["ms_device_l2_warm"] = back_to_back(torch, stream, call)
                 if op in ("vmul", "axpy"):
                     entry["modmul/s"] = entry["elements/s"]
                 res[f"{op}_{bits}" if log2n == 24 else f"{op}_{bits}_n2^{log2n}"] = entry
