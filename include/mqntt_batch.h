@@ -47,8 +47,9 @@ typedef struct mq_job {
 
 /* batch creation options; zero-initialised fields take the defaults */
 typedef struct mq_batch_opts {
-    unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit -- 2, or 3 for batches of 64-bit
-                              transforms only; larger values are clamped to that) */
+    unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit -- 3 with the prefetching form,
+                              4 for batches of 64-bit transforms only; 2 and 3 with the split form;
+                              larger values are clamped to that) */
     unsigned lag;          /* pipeline lag between dependent stages, in waves of the persistent grid (0: 8) */
     unsigned blas_chunk;   /* residues per BLAS work item (0: 16384); a multiple of 2048 */
     double wait_timeout_s; /* limit of every device-side wait (0: 2 s) */
@@ -102,7 +103,7 @@ int mq_batch_info(const mq_batch *b, size_t *items, unsigned *ctas, size_t *ntt_
 int mq_batch_destroy(mq_batch *b);
 
 /*
- * Autotuner: time candidate options (CTAs per SM, pipeline lag, BLAS chunk) on this batch shape
+ * Autotuner: time candidate options (kernel form, CTAs per SM, pipeline lag, BLAS chunk) on this batch shape
  * with a few launches each, write the fastest to *best and, if cache_path is non-NULL, record it
  * in that JSON cache under a key made of the device name and the batch shape.  The jobs' buffers
  * are overwritten (the timing runs the batch).  Errors: those of mq_batch_create.
