@@ -166,8 +166,8 @@ __device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned
 // WM: residue widths present (bit 0: 64-bit, bit 1: 128-bit); BL: BLAS jobs present.  A batch runs
 // the narrowest instantiation that covers its jobs, which keeps registers and code small.  64-bit
 // transforms alone need fewer registers and half the shared memory, and their arithmetic has
-// shorter dependency chains per residue, so that instantiation runs three CTAs per SM to keep more
-// warps in flight.
+// shorter dependency chains per residue, so that instantiation runs one CTA per SM more (three in
+// the split form, four in the prefetching form) to keep more warps in flight.
 template <int WM, bool BL>
 struct KCfg {
     static constexpr int MINB = (WM == 1 && !BL) ? 3 : 2;  // resident CTAs per SM the registers allow

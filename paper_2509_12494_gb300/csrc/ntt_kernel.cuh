@@ -17,6 +17,8 @@
 //     (G consecutive columns give G-residue contiguous segments in global memory);
 //   * inside a tile each thread holds R = 8 residues in registers and runs 3 stages on them
 //     (radix-8), then the tile is exchanged through shared memory for the next 3 stages;
+//   * a pass too small to give every SM a CTA takes the latency shape instead: one tile per CTA,
+//     R = 4 (radix-4 rounds on more threads), the tile's twiddles staged in shared memory;
 //   * natural-order output (or input, for the inverse) is a bit-reversal permutation folded into
 //     the row pass' global addresses, with tiles chosen so that every CTA still writes contiguous
 //     segments; the two passes then go through a scratch buffer because the permutation is not
