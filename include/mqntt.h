@@ -66,6 +66,20 @@ extern "C" {
 #define MQ_ORDER_NATURAL 0u /* transformed side in natural order: position k holds yhat_k */
 #define MQ_ORDER_BITREV 2u  /* transformed side in bit-reversed order: position i holds yhat_brv(i) */
 
+/*
+ * Input checking (Sec. 2.1: the modular operations are defined for canonical operands, 0 <= a, b < q).
+ * As a plan flag, every ntt_forward / ntt_inverse / ntt_polymul call on the plan first checks that
+ * the residues it will read (the first N of each polynomial; a and b for the product) are below q.
+ * OR-ed into the `width` argument of a BLAS call (for example MQ_W128 | MQ_CHECK_INPUTS), the call
+ * checks its inputs (a and b; axpy: x and y).  A checked call runs a read-only range-check kernel on
+ * its stream, reads the result back (it synchronises the stream, so it cannot be captured in a
+ * graph) and returns MQ_ERR_RANGE, naming the operand, without running the operation when a residue
+ * is >= q: the outputs are then untouched.  ntt_forward_noalloc refuses checked plans (the check
+ * needs a result word of device memory).  Batched jobs: see mqntt_batch.h.  Unchecked calls are
+ * unchanged: non-canonical inputs give unspecified (but memory-safe) results.
+ */
+#define MQ_CHECK_INPUTS 0x100u
+
 typedef struct ntt_plan ntt_plan;
 
 /*
@@ -76,7 +90,8 @@ typedef struct ntt_plan ntt_plan;
  * The plan validates q and the root's exact order, then builds device-resident twiddle tables
  * (N entries per direction, each a power of the root and its Shoup companion) on `stream`; the
  * call returns after they are built.  `q` and `root` are two words each, low first.
- * log2n in [1, 24].  The plan owns its device memory until ntt_plan_destroy.
+ * log2n in [1, 24].  flags: MQ_CYCLIC, MQ_ORDER_BITREV and MQ_CHECK_INPUTS, OR-ed.  The plan
+ * owns its device memory until ntt_plan_destroy.
  * Errors: MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
  */
 int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[2], const uint64_t root[2], int width,
@@ -90,7 +105,7 @@ int ntt_plan_destroy(ntt_plan *plan);
  * of d_data (stride >= N when batch > 1).  Input in natural coefficient order; output in the
  * plan's order.  batch == 0 is a no-op.  Natural-order transforms with N > 2^12 stage through a
  * temporary device buffer of batch * N residues taken from the library's stream-ordered pool.
- * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
+ * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA; MQ_ERR_RANGE (checked plans).
  */
 int ntt_forward(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
 
@@ -113,7 +128,7 @@ int ntt_inverse(const ntt_plan *plan, void *d_data, size_t batch, size_t stride,
  * the result is canonical, in natural order.  d_c may be d_a or d_b (in place); other overlaps
  * are undefined.  a and b are not modified unless c is one of them.  For N > 2^12 the call takes
  * batch * N residues of stream-ordered scratch from the library's pool.  batch == 0 is a no-op.
- * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA.
+ * Errors: MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_SIZE, MQ_ERR_OOM, MQ_ERR_CUDA; MQ_ERR_RANGE (checked plans).
  */
 int ntt_polymul(const ntt_plan *plan, void *d_c, const void *d_a, const void *d_b, size_t batch, size_t stride,
                 void *stream);
@@ -132,7 +147,8 @@ int ntt_polymul(const ntt_plan *plan, void *d_c, const void *d_a, const void *d_
  * each device looks up the buffer's device address (cudaGetSymbolAddress, which may load the
  * library's device code); make that first call before any stream capture.
  * Errors: those of ntt_forward, except MQ_ERR_OOM; MQ_ERR_SIZE for an oversized batch;
- * MQ_ERR_ARG if the plan belongs to another device than the current one.
+ * MQ_ERR_ARG if the plan belongs to another device than the current one or was created with
+ * MQ_CHECK_INPUTS.
  */
 #define MQ_NOALLOC_SCRATCH_BYTES (16u << 20) /* 16 MiB */
 int ntt_forward_noalloc(const ntt_plan *plan, void *d_data, size_t batch, size_t stride, void *stream);
@@ -144,8 +160,9 @@ int ntt_plan_info(const ntt_plan *plan, unsigned *log2n, int *width, unsigned *f
  * Element-wise modular BLAS over n residues (Sec. 2.3; modular ring operations of Sec. 2.1, Eq. 1).
  *   mod_vadd: c_i = a_i + b_i mod q      mod_vsub: c_i = a_i - b_i mod q
  *   mod_vmul: c_i = a_i * b_i mod q      mod_axpy: y_i = a * x_i + y_i mod q (scalar a < q)
- * Any n (0 is a no-op).  The output may alias any input.  Errors: MQ_ERR_ARG, MQ_ERR_MODULUS,
- * MQ_ERR_ALIGN, MQ_ERR_CUDA.
+ * Any n (0 is a no-op).  The output may alias any input.  `width` may carry MQ_CHECK_INPUTS (see
+ * above).  Errors: MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ALIGN, MQ_ERR_CUDA; MQ_ERR_RANGE (scalar a not
+ * below q, or a checked input residue not below q).
  */
 int mod_vadd(void *d_c, const void *d_a, const void *d_b, size_t n, const uint64_t q[2], int width, void *stream);
 int mod_vsub(void *d_c, const void *d_a, const void *d_b, size_t n, const uint64_t q[2], int width, void *stream);

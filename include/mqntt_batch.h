@@ -12,6 +12,14 @@
  *
  * Requirements: NTT jobs need 2^6 <= N <= 2^22 (use ntt_forward / ntt_inverse otherwise); all
  * device pointers aligned to 16 bytes; BLAS 64-bit residues of length >= 1.
+ *
+ * Input checking (MQ_CHECK_INPUTS of mqntt.h; Sec. 2.1's canonical operands): NTT jobs whose plan
+ * carries the flag and BLAS jobs whose `width` carries it (width = MQ_W128 | MQ_CHECK_INPUTS) have
+ * their inputs range-checked by a kernel in the launch, before any job runs.  If a residue is >= q,
+ * no job of the batch runs (every output is untouched) and mq_batch_status returns MQ_ERR_RANGE.
+ * The check sees the buffers as they are when the launch starts: an input that an earlier job of
+ * the same batch writes is checked as it was before the batch.  The server (mqntt_serve.h) does not
+ * take checked jobs.
  */
 #ifndef MQNTT_BATCH_H
 #define MQNTT_BATCH_H
@@ -91,8 +99,9 @@ int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, void *stream)
 int mq_batch_launch(mq_batch *b, void *stream);
 
 /*
- * Wait for the last launch and return its device status: MQ_OK, or MQ_ERR_TIMEOUT when a bounded
- * device-side wait gave up (the batch's results are then incomplete; the device stays usable).
+ * Wait for the last launch and return its device status: MQ_OK, MQ_ERR_TIMEOUT when a bounded
+ * device-side wait gave up (the batch's results are then incomplete; the device stays usable), or
+ * MQ_ERR_RANGE when the input check of a checked job failed (no job ran).
  */
 int mq_batch_status(mq_batch *b);
 

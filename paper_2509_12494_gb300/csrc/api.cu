@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "../../include/mqntt.h"
+#include "check.h"
 #include "common.cuh"
 #include "hostmath.h"
 #include "plan.h"
@@ -57,11 +58,12 @@ int mq_check_modulus(const uint64_t q[2], int width, hm::u128 *qv) {
 // alignment a residue array needs: its vector loads (one word for 192-bit residues)
 static unsigned align_of(int width) { return width == 3 ? 8u : 8u * (unsigned)width; }
 
-static int check_ptr(const void *p, int width, const char *name) {
+int mq_check_ptr(const void *p, int width, const char *name) {
     if (!p) return mq_fail(MQ_ERR_ARG, "%s is NULL", name);
     if (((uintptr_t)p) % align_of(width)) return mq_fail(MQ_ERR_ALIGN, "%s is not %u-byte aligned", name, align_of(width));
     return MQ_OK;
 }
+static int check_ptr(const void *p, int width, const char *name) { return mq_check_ptr(p, width, name); }
 
 // residues of three and four words: q odd, 3 <= q < 2^(64 width - 4), so that 16q fits the word
 static int check_modulus_wide(const uint64_t *q, int width, hw::U *qv) {
@@ -185,7 +187,7 @@ extern "C" int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[
     if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!root) return mq_fail(MQ_ERR_ARG, "root is NULL");
-    if (flags & ~(MQ_CYCLIC | MQ_ORDER_BITREV)) return mq_fail(MQ_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (flags & ~(MQ_CYCLIC | MQ_ORDER_BITREV | MQ_CHECK_INPUTS)) return mq_fail(MQ_ERR_ARG, "unknown flag bits 0x%x", flags);
     if (log2n < 1 || log2n > 24) return mq_fail(MQ_ERR_SIZE, "log2n must be in [1, 24], got %u", log2n);
     if (width == MQ_W192 || width == MQ_W256)
         return plan_create_wide(out, log2n, q, root, width, flags, (cudaStream_t)stream);
@@ -291,6 +293,11 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
     if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
     if (batch > (SIZE_MAX / 32) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->flags & MQ_CHECK_INPUTS) {
+        const CheckRec r = check_rec(d, batch, N, stride, p->width, p->q, "d_data");
+        rc = range_check(&r, 1, s);
+        if (rc) return rc;
+    }
     const bool natural = !(p->flags & MQ_ORDER_BITREV);
     const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
 
@@ -382,6 +389,12 @@ extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void
     if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
     if (batch > (SIZE_MAX / 16) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->flags & MQ_CHECK_INPUTS) {
+        const CheckRec r[2] = {check_rec(a, batch, N, stride, p->width, p->q, "d_a"),
+                               check_rec(b, batch, N, stride, p->width, p->q, "d_b")};
+        rc = range_check(r, 2, s);
+        if (rc) return rc;
+    }
     const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
     MulArgs m;
     memcpy(m.q, p->q, sizeof m.q);
@@ -446,8 +459,15 @@ extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void
 // BLAS
 // ------------------------------------------------------------------------------------------------
 
+// The input check of a BLAS call: a and b (axpy: x and y).
+static int blas_check(int op, const void *a, const void *b, size_t n, const uint64_t *q, int width, cudaStream_t s) {
+    const CheckRec r[2] = {check_rec(a, 1, n, n, width, q, op == OP_AXPY ? "d_x" : "d_a"),
+                           check_rec(b, 1, n, n, width, q, op == OP_AXPY ? "d_y" : "d_b")};
+    return range_check(r, 2, s);
+}
+
 static int blas_wide(int op, void *c, const void *a, const void *b, size_t n, const uint64_t *q, int width,
-                     const uint64_t *scalar, void *stream) {
+                     const uint64_t *scalar, bool checked, void *stream) {
     hw::U Q;
     int rc = check_modulus_wide(q, width, &Q);
     if (rc) return rc;
@@ -472,13 +492,16 @@ static int blas_wide(int op, void *c, const void *a, const void *b, size_t n, co
         hw::to_words(sv, args.s, width);
         hw::to_words(hw::shoup(sv, Q, 64 * width), args.sp, width);
     }
+    if (checked && (rc = blas_check(op, a, b, n, q, width, (cudaStream_t)stream))) return rc;
     cudaError_t e = launch_blas_wide(width, op, args, (cudaStream_t)stream);
     return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "BLAS launch");
 }
 
-static int blas(int op, void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width,
+static int blas(int op, void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width_arg,
                 const uint64_t *scalar, void *stream) {
-    if (width == MQ_W192 || width == MQ_W256) return blas_wide(op, c, a, b, n, q, width, scalar, stream);
+    const bool checked = ((unsigned)width_arg & MQ_CHECK_INPUTS) != 0;
+    const int width = (int)((unsigned)width_arg & ~MQ_CHECK_INPUTS);
+    if (width == MQ_W192 || width == MQ_W256) return blas_wide(op, c, a, b, n, q, width, scalar, checked, stream);
     hm::u128 Q;
     int rc = mq_check_modulus(q, width, &Q);
     if (rc) return rc;
@@ -504,6 +527,7 @@ static int blas(int op, void *c, const void *a, const void *b, size_t n, const u
         hm::to_words(s, args.s);
         hm::to_words(hm::shoup(s, Q, width == MQ_W64 ? 64 : 128), args.sp);
     }
+    if (checked && (rc = blas_check(op, a, b, n, args.q, width, (cudaStream_t)stream))) return rc;
     cudaError_t e = launch_blas(width, op, args, (cudaStream_t)stream);
     return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "BLAS launch");
 }

@@ -81,7 +81,11 @@ struct mq_batch {
     cudaEvent_t done = nullptr, staged = nullptr;
     int *h_status = nullptr;
     bool launched = false;
+    CheckRec *dcheck = nullptr;        // operands of the jobs that carry MQ_CHECK_INPUTS (device table)
+    unsigned n_check = 0;
+    unsigned long long check_max = 0;  // residues of the largest checked operand
 };
+
 
 static int job_passes(const mq_job &j) {
     if (j.kind == MQ_JOB_NTT_FORWARD || j.kind == MQ_JOB_NTT_INVERSE) return j.plan->log2n <= 11 ? 1 : 2;
@@ -89,6 +93,27 @@ static int job_passes(const mq_job &j) {
 }
 
 static bool is_ntt(int kind) { return kind == MQ_JOB_NTT_FORWARD || kind == MQ_JOB_NTT_INVERSE; }
+
+// The operands a launch checks before any job runs: the data of NTT jobs whose plan carries
+// MQ_CHECK_INPUTS, both inputs of BLAS jobs whose width carries it (axpy: x and y).
+static void check_records(const mq_job *jobs, size_t njobs, std::vector<CheckRec> &out, unsigned long long &max_res) {
+    out.clear();
+    max_res = 0;
+    for (size_t i = 0; i < njobs; ++i) {
+        const mq_job &j = jobs[i];
+        if (is_ntt(j.kind)) {
+            if (!(j.plan->flags & MQ_CHECK_INPUTS)) continue;
+            const size_t N = (size_t)1 << j.plan->log2n, batch = j.batch ? j.batch : 1;
+            out.push_back(check_rec(j.data, batch, N, batch == 1 ? N : j.stride, j.plan->width, j.plan->q, "job data"));
+            max_res = std::max<unsigned long long>(max_res, (unsigned long long)batch * N);
+        } else if ((unsigned)j.width & MQ_CHECK_INPUTS) {
+            const int w = (int)((unsigned)j.width & ~MQ_CHECK_INPUTS);
+            out.push_back(check_rec(j.a, 1, j.n, j.n, w, j.q, "job input a"));
+            out.push_back(check_rec(j.kind == MQ_JOB_AXPY ? j.data : j.b, 1, j.n, j.n, w, j.q, "job input b"));
+            max_res = std::max<unsigned long long>(max_res, j.n);
+        }
+    }
+}
 
 static int blas_op_of(int kind) {
     switch (kind) {
@@ -188,8 +213,9 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
         return MQ_OK;
     }
     if (j.kind < MQ_JOB_VADD || j.kind > MQ_JOB_AXPY) return mq_fail(MQ_ERR_ARG, "job %zu: unknown kind %d", index, j.kind);
+    const int width = (int)((unsigned)j.width & ~MQ_CHECK_INPUTS);  // the check flag rides on the width
     hm::u128 Q;
-    int rc = mq_check_modulus(j.q, j.width, &Q);
+    int rc = mq_check_modulus(j.q, width, &Q);
     if (rc) return rc;
     if (j.n == 0) return mq_fail(MQ_ERR_ARG, "job %zu: empty vector", index);
     const void *ptrs[3] = {j.data, j.a, j.kind == MQ_JOB_AXPY ? j.data : j.b};
@@ -198,7 +224,7 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
         if (((uintptr_t)ptrs[k]) % 16) return mq_fail(MQ_ERR_ALIGN, "job %zu: operands must be 16-byte aligned", index);
     }
     d.kind = JK_BLAS;
-    d.width = j.width;
+    d.width = width;
     d.op = blas_op_of(j.kind);
     d.chunk = o.blas_chunk;
     BlasArgs &b = d.ba;
@@ -211,9 +237,9 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
     hm::to_words(hm::barrett_mu(Q, b.L), b.mu);
     if (j.kind == MQ_JOB_AXPY) {
         hm::u128 s = hm::from_words(j.scalar);
-        if (s >= Q || (j.width == MQ_W64 && j.scalar[1])) return mq_fail(MQ_ERR_RANGE, "job %zu: scalar must be < q", index);
+        if (s >= Q || (width == MQ_W64 && j.scalar[1])) return mq_fail(MQ_ERR_RANGE, "job %zu: scalar must be < q", index);
         hm::to_words(s, b.s);
-        hm::to_words(hm::shoup(s, Q, j.width == MQ_W64 ? 64 : 128), b.sp);
+        hm::to_words(hm::shoup(s, Q, width == MQ_W64 ? 64 : 128), b.sp);
     }
     return MQ_OK;
 }
@@ -382,7 +408,7 @@ int mq::batch_detail::job_variant(const mq_job *jobs, size_t njobs) {
     int v = 0;
     for (size_t i = 0; i < njobs; ++i) {
         const bool ntt = is_ntt(jobs[i].kind);
-        const int w = ntt ? (jobs[i].plan ? jobs[i].plan->width : 2) : jobs[i].width;
+        const int w = ntt ? (jobs[i].plan ? jobs[i].plan->width : 2) : (int)((unsigned)jobs[i].width & ~MQ_CHECK_INPUTS);
         v |= (w == MQ_W64 ? 1 : 2) | (ntt ? 0 : 4);
     }
     return v ? v : 3;
@@ -429,9 +455,14 @@ int mq::batch_detail::persistent_grid(int variant, int form, unsigned ctas_per_s
 cudaError_t mq::batch_detail::launch_persistent(int variant, int form, const JobDev *djobs, const ItemDev *ditems,
                                                 unsigned n_items, unsigned *dctrs, size_t n_ctrs, unsigned njobs,
                                                 unsigned long long limit_ns, unsigned grid, size_t smem,
-                                                cudaStream_t s) {
+                                                cudaStream_t s, const CheckRec *dcheck, unsigned n_check,
+                                                unsigned long long check_max) {
     cudaError_t e = cudaMemsetAsync(dctrs, 0, n_ctrs * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    if (n_check) {  // a failed input check ends the item counter, so no job runs
+        e = launch_batch_check(dcheck, n_check, check_max, dctrs, n_items, s);
+        if (e != cudaSuccess) return e;
+    }
     const int k = kernel_slot(variant);
 #define MQ_LAUNCH(F, WM, BL) return PersistentKernel<F, WM, BL>::launch(djobs, ditems, n_items, dctrs, njobs, limit_ns, grid, smem, s)
     if (form) {
@@ -460,6 +491,7 @@ static void destroy_batch(mq_batch *b) {
     if (b->djobs) cudaFree(b->djobs);
     if (b->ditems) cudaFree(b->ditems);
     if (b->dctrs) cudaFree(b->dctrs);
+    if (b->dcheck) cudaFree(b->dcheck);
     for (void *p : b->scratch)
         if (p) cudaFree(p);
     delete b;
@@ -467,7 +499,8 @@ static void destroy_batch(mq_batch *b) {
 
 static int enqueue_run(mq_batch *b, cudaStream_t s) {
     cudaError_t e = launch_persistent(b->variant, b->form, b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
-                                      (unsigned)b->hjobs.size(), b->limit_ns, b->grid, b->smem, s);
+                                      (unsigned)b->hjobs.size(), b->limit_ns, b->grid, b->smem, s, b->dcheck, b->n_check,
+                                      b->check_max);
     if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
     e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return mq_cuda_fail(e, "status copy");
@@ -540,6 +573,23 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
         destroy_batch(b);
         return mq_cuda_fail(e, "batch table upload");
     }
+    {
+        std::vector<CheckRec> recs;
+        check_records(jobs, njobs, recs, b->check_max);
+        if (!recs.empty()) {
+            if ((e = cudaMalloc(&b->dcheck, recs.size() * sizeof(CheckRec))) != cudaSuccess) {
+                cudaGetLastError();
+                destroy_batch(b);
+                return mq_fail(MQ_ERR_OOM, "input check table does not fit");
+            }
+            if ((e = cudaMemcpy(b->dcheck, recs.data(), recs.size() * sizeof(CheckRec), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+                destroy_batch(b);
+                return mq_cuda_fail(e, "input check table upload");
+            }
+            b->n_check = (unsigned)recs.size();
+        }
+    }
     if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess) {
@@ -587,6 +637,14 @@ extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, vo
     if ((e = cudaMemcpyAsync(b->djobs, b->pinned_jobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaEventRecord(b->staged, s)) != cudaSuccess)
         return mq_cuda_fail(e, "job table upload");
+    if (b->n_check) {  // same shapes, so the same operands are checked: only their pointers change
+        std::vector<CheckRec> recs;
+        unsigned long long mx = 0;
+        check_records(jobs, njobs, recs, mx);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
+            (e = cudaMemcpy(b->dcheck, recs.data(), recs.size() * sizeof(CheckRec), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return mq_cuda_fail(e, "input check table upload");
+    }
     for (size_t i = 0; i < njobs; ++i) b->shape[i] = jobs[i];
     return MQ_OK;
 }
@@ -614,6 +672,7 @@ extern "C" int mq_batch_status(mq_batch *b) {
     cudaError_t e = cudaEventSynchronize(b->done);
     if (e != cudaSuccess) return mq_cuda_fail(e, "batch wait");
     int st = *(volatile int *)b->h_status;
+    if (st == MQ_ERR_RANGE) return mq_fail(st, "an input residue of a checked job is not below q: no job of the batch ran");
     if (st != 0) return mq_fail(st, "a device-side wait of the batch gave up after %.3f s", b->opts.wait_timeout_s);
     return MQ_OK;
 }

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/mqntt_batch.h"
+#include "check.h"
 #include "common.cuh"
 
 namespace mq {
@@ -86,11 +87,13 @@ int kernel_form(int variant, unsigned flags);
 // fit) on the current device, and the bytes of one tile buffer.
 int persistent_grid(int variant, int form, unsigned ctas_per_sm, unsigned *grid, size_t *smem);
 
-// Zero the counters and launch the persistent kernel instantiation that covers `variant` (the
-// tables' variant) on `s` (asynchronous).
+// Zero the counters, run the input check of the n_check operands in dcheck (if any; check_max is the
+// largest one's residue count), and launch the persistent kernel instantiation that covers
+// `variant` (the tables' variant) on `s` (asynchronous).
 cudaError_t launch_persistent(int variant, int form, const JobDev *djobs, const ItemDev *ditems, unsigned n_items,
                               unsigned *dctrs, size_t n_ctrs, unsigned njobs, unsigned long long limit_ns,
-                              unsigned grid, size_t smem, cudaStream_t s);
+                              unsigned grid, size_t smem, cudaStream_t s, const CheckRec *dcheck = nullptr,
+                              unsigned n_check = 0, unsigned long long check_max = 0);
 
 void apply_defaults(mq_batch_opts &o);
 

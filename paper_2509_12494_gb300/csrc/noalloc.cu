@@ -17,6 +17,7 @@
 
 int mq_fail(int code, const char *fmt, ...);
 int mq_cuda_fail(cudaError_t e, const char *where);
+int mq_check_ptr(const void *p, int width, const char *name);  // the alignment rule of every entry point
 
 using namespace mq;
 
@@ -63,20 +64,23 @@ static PassArgs noalloc_pass(const ntt_plan *p, size_t batch) {
 
 extern "C" int ntt_forward_noalloc(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
     if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
+    if (p->flags & MQ_CHECK_INPUTS)
+        return mq_fail(MQ_ERR_ARG, "ntt_forward_noalloc does not run the input check: use a plan without MQ_CHECK_INPUTS");
     if (batch == 0) return MQ_OK;
-    if (!d) return mq_fail(MQ_ERR_ARG, "d_data is NULL");
-    if (((uintptr_t)d) % (8u * (unsigned)p->width)) return mq_fail(MQ_ERR_ALIGN, "d_data is not %d-byte aligned", 8 * p->width);
+    int rc = mq_check_ptr(d, p->width, "d_data");
+    if (rc) return rc;
     int dev = 0;
-    cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "cudaGetDevice");
     if (dev != p->device) return mq_fail(MQ_ERR_ARG, "the plan belongs to device %d, device %d is current", p->device, dev);
     const size_t N = (size_t)1 << p->log2n;
     if (batch == 1) stride = N;
     if (stride < N) return mq_fail(MQ_ERR_SIZE, "stride %zu is shorter than N = %zu", stride, N);
-    if (batch > (SIZE_MAX / 16) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
+    // the bound of ntt_forward: batch * stride residues of up to 32 bytes stay addressable
+    if (batch > (SIZE_MAX / 32) / stride) return mq_fail(MQ_ERR_ARG, "batch * stride overflows");
     cudaStream_t s = (cudaStream_t)stream;
     const bool natural = !(p->flags & MQ_ORDER_BITREV);
     const int logN = (int)p->log2n, L1 = p->L1, L2 = logN - L1;
-    cudaError_t e;
 
     if (L1 == 0) {  // one pass, in place: no staging
         PassArgs a = noalloc_pass(p, batch);
@@ -91,13 +95,14 @@ extern "C" int ntt_forward_noalloc(const ntt_plan *p, void *d, size_t batch, siz
 
     void *scr = nullptr;
     if (natural) {
+        // batch * N <= batch * stride < SIZE_MAX / 32 (checked above), so this product cannot wrap
         const size_t need = batch * N * 8u * (size_t)p->width;
         if (need > (size_t)MQ_NOALLOC_SCRATCH_BYTES)
             return mq_fail(MQ_ERR_SIZE,
                            "ntt_forward_noalloc: %zu polynomials of N = %zu need %zu staging bytes, the static "
                            "buffer holds %zu; split the batch",
                            batch, N, need, (size_t)MQ_NOALLOC_SCRATCH_BYTES);
-        int rc = noalloc_scratch(&scr);
+        rc = noalloc_scratch(&scr);
         if (rc) return rc;
     }
     PassArgs col = noalloc_pass(p, batch), row = noalloc_pass(p, batch);

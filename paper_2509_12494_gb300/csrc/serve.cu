@@ -396,6 +396,10 @@ extern "C" int mq_submit(mq_server *srv, const mq_job *job, uint64_t *ticket) {
     Server *s = srv->impl;
     if (job->after != -1) return mq_fail(MQ_ERR_ARG, "served jobs are independent: `after` must be -1");
     if (is_ntt_kind(job->kind) && !job->plan) return mq_fail(MQ_ERR_ARG, "NTT job without a plan");
+    // a failed check would fail every request batched with this one: served jobs are not checked
+    if ((is_ntt_kind(job->kind) && (job->plan->flags & MQ_CHECK_INPUTS)) ||
+        (!is_ntt_kind(job->kind) && ((unsigned)job->width & MQ_CHECK_INPUTS)))
+        return mq_fail(MQ_ERR_ARG, "the server does not take jobs with MQ_CHECK_INPUTS: check inputs before submitting");
     {
         int rc = check_job(*job, s->opts);  // everything a batch would check about this job
         if (rc) return rc;

@@ -23,6 +23,7 @@ MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_ALIGN = -1, -2, -3,
 MQ_ERR_OOM, MQ_ERR_CUDA, MQ_ERR_TIMEOUT, MQ_ERR_RANGE, MQ_ERR_STATE = -6, -7, -8, -9, -10
 MQ_W64, MQ_W128, MQ_W192, MQ_W256 = 1, 2, 3, 4
 MQ_NEGACYCLIC, MQ_CYCLIC, MQ_ORDER_NATURAL, MQ_ORDER_BITREV = 0, 1, 0, 2
+MQ_CHECK_INPUTS = 0x100   # plan flag, or OR-ed into a BLAS width: range-check the inputs first
 
 _u64x2 = ctypes.c_uint64 * 2
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -103,7 +104,7 @@ def load(build_if_missing: bool = False):
 def words(v: int, width: int = 2) -> "ctypes.Array":
     """v as max(width, 2) 64-bit words, low first (the ABI's modulus / root / scalar arrays)."""
     v = int(v)
-    n = max(width, 2)
+    n = max(width & 0xFF, 2)   # a width may carry MQ_CHECK_INPUTS
     if v < 0 or v >= 2 ** (64 * n):
         raise ValueError(f"value must be in [0, 2^{64 * n})")
     return (ctypes.c_uint64 * n)(*[(v >> (64 * k)) & (2**64 - 1) for k in range(n)])

@@ -122,3 +122,23 @@ def test_wide_plan_rejects_without_touching_the_device(lib):
         with pytest.raises(M.MqError) as e:
             M.ntt_plan_create(args["log2n"], args["q"], args["root"], args["width"], args["flags"], stream=0)
         assert e.value.code == code, (kw, M.mq_last_error())
+
+
+def test_check_flag_matches_the_header():
+    """MQ_CHECK_INPUTS is one value for plan flags and BLAS widths, distinct from every width and
+    order flag, and the binding's constant is the header's."""
+    text = open(os.path.join(ROOT, "include", "mqntt.h")).read()
+    m = re.search(r"#define MQ_CHECK_INPUTS (0x[0-9a-fA-F]+)u", text)
+    assert m and int(m.group(1), 16) == M.MQ_CHECK_INPUTS
+    assert M.MQ_CHECK_INPUTS & (M.MQ_CYCLIC | M.MQ_ORDER_BITREV | 0xFF) == 0
+    assert all((w | M.MQ_CHECK_INPUTS) & 0xFF == w for w in (M.MQ_W64, M.MQ_W128, M.MQ_W192, M.MQ_W256))
+
+
+def test_checked_blas_still_rejects_bad_arguments_first(lib):
+    """Argument errors come before the device check (which would need a GPU)."""
+    with pytest.raises(M.MqError) as e:   # even modulus, checked width
+        M.mod_vmul(16, 16, 16, 4, 2**61, M.MQ_W128 | M.MQ_CHECK_INPUTS, stream=0)
+    assert e.value.code == M.MQ_ERR_MODULUS
+    with pytest.raises(M.MqError) as e:   # misaligned pointer
+        M.mod_vadd(8, 16, 16, 4, 2**61 + 1, M.MQ_W128 | M.MQ_CHECK_INPUTS, stream=0)
+    assert e.value.code == M.MQ_ERR_ALIGN

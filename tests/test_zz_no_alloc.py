@@ -48,3 +48,47 @@ def test_noalloc_rejects_batches_beyond_the_buffer(mq):
         mq.ntt_forward_noalloc(plan, d, 17, 1 << 16)
     assert e.value.code == mq.MQ_ERR_SIZE
     assert "split the batch" in mq.mq_last_error()
+
+
+def _laid_out(mq, x, batch, N, stride, width, off_words):
+    """A device buffer holding `batch` polynomials `stride` residues apart, starting `off_words`
+    64-bit words into the allocation; every other word holds a marker.  Returns (buffer, view)."""
+    import torch
+    total = off_words + batch * stride * width + 8
+    host = np.full(total, 0x5A5A5A5A5A5A5A5A, dtype=np.uint64)
+    xs = x.reshape(batch, N * width)
+    for b in range(batch):
+        s = off_words + b * stride * width
+        host[s:s + N * width] = xs[b]
+    buf = mq.to_device(host)
+    view = buf[off_words:off_words + batch * stride * width]
+    return buf, view
+
+
+@pytest.mark.parametrize("width,bits,log2n,batch,stride_pad,off_words", [
+    (3, 188, 14, 4, 0, 1),    # 192-bit residues at an address that is 8- but not 24-byte aligned
+    (4, 252, 14, 3, 0, 4),    # 256-bit residues at a 32-byte offset
+    (2, 124, 14, 4, 64, 0),   # stride N + 64: staging uses N, the output goes back to the caller's stride
+    (1, 60, 15, 3, 3, 1),     # 64-bit residues, odd stride, 8-byte offset
+])
+def test_noalloc_layouts_match_ntt_forward(mq, width, bits, log2n, batch, stride_pad, off_words):
+    """Offsets and strides the staging must respect: the results equal ntt_forward's on the same
+    layout, bit for bit, and the words between polynomials stay untouched."""
+    import torch
+    q = W.gen_prime(bits, log2n + 1, 9)
+    psi = W.gen_root(q, log2n, 9)
+    N = 1 << log2n
+    stride = N + stride_pad
+    plan = mq.ntt_plan_create(log2n, q, psi, width, 0)
+    for call in range(2):
+        x = W.gen_residues(batch * N, q, seed=300 + call, width=width)
+        buf_a, view_a = _laid_out(mq, x, batch, N, stride, width, off_words)
+        buf_b, view_b = _laid_out(mq, x, batch, N, stride, width, off_words)
+        mq.ntt_forward(plan, view_a, batch, stride)
+        mq.ntt_forward_noalloc(plan, view_b, batch, stride)
+        torch.cuda.synchronize()
+        want, got = mq.to_host(buf_a), mq.to_host(buf_b)
+        assert np.array_equal(got, want), f"call {call}"
+        before, _ = _laid_out(mq, x, batch, N, stride, width, off_words)
+        marker = mq.to_host(before) == np.uint64(0x5A5A5A5A5A5A5A5A)
+        assert np.array_equal(got[marker], mq.to_host(before)[marker]), "padding between polynomials changed"
