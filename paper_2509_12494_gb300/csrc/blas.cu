@@ -82,14 +82,25 @@ __global__ void __launch_bounds__(BLAS_THREADS) blas64_kernel(uint64_t *c, const
     for (size_t i = done + tid; i < n; i += nt) c[i] = op64<OP>(a[i], b[i], m, s, sp);
 }
 
+// One wave: at most the CTAs of the kernel (width W, op OP) that are resident at once on the device
+// (looked up once per kernel), so that no CTA waits for a second wave and the grid-stride loop
+// covers the rest.
+template <int W, int OP>
 unsigned blas_grid(size_t work) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-    size_t per_block = (size_t)BLAS_THREADS * BLAS_UNROLL;
+    static int per_sm = 0, sms = 0;  // benign race: every thread computes the same values
+    if (per_sm == 0) {
+        int dev = 0, n = 0, m = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        const cudaError_t e = W == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blas128_kernel<OP>, BLAS_THREADS, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blas64_kernel<OP>, BLAS_THREADS, 0);
+        if (e != cudaSuccess || n < 1) n = 1;
+        sms = m > 0 ? m : 1;
+        per_sm = n;
+    }
+    const size_t per_block = (size_t)BLAS_THREADS * BLAS_UNROLL;
     size_t want = (work + per_block - 1) / per_block;
-    size_t cap = (size_t)sms * 8;  // grid-stride beyond eight resident CTAs per SM
+    const size_t cap = (size_t)sms * per_sm;
     if (want > cap) want = cap;
     return want ? (unsigned)want : 1u;
 }
@@ -99,12 +110,12 @@ cudaError_t launch_op(int width, const BlasArgs &a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (width == 2) {
         Mod128 m{u4(a.q), u4(a.mu), a.L};
-        blas128_kernel<OP><<<blas_grid(a.n), BLAS_THREADS, 0, s>>>((uint4 *)a.c, (const uint4 *)a.a,
-                                                                   (const uint4 *)a.b, a.n, m, u4(a.s), u4(a.sp));
+        blas128_kernel<OP><<<blas_grid<2, OP>(a.n), BLAS_THREADS, 0, s>>>(
+            (uint4 *)a.c, (const uint4 *)a.a, (const uint4 *)a.b, a.n, m, u4(a.s), u4(a.sp));
     } else {
         Mod64 m{a.q[0], a.mu[0], a.L};
         int vec = ((((uintptr_t)a.a) | ((uintptr_t)a.b) | ((uintptr_t)a.c)) & 15) == 0;
-        blas64_kernel<OP><<<blas_grid(vec ? a.n / 2 : a.n), BLAS_THREADS, 0, s>>>(
+        blas64_kernel<OP><<<blas_grid<1, OP>(vec ? a.n / 2 : a.n), BLAS_THREADS, 0, s>>>(
             (uint64_t *)a.c, (const uint64_t *)a.a, (const uint64_t *)a.b, a.n, m, a.s[0], a.sp[0], vec);
     }
     return cudaGetLastError();
