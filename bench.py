@@ -38,6 +38,57 @@ HBM_FALLBACK_GBS = 6800.0
 # copy) are paid once per job, as in a serving loop that runs continuously
 E2E_STEPS = 32
 E2E_JOBS = 3      # the e2e figure is the median of this many jobs (the host link's rate varies)
+# algorithmic 32-bit multiply instructions (lo and hi halves of 32 x 32 limb products) per Shoup
+# product: 124-bit residues 30 limb products = 60; 64-bit residues: lo(a w) 4 + hi(a w') 8 + lo(qhat q) 4
+MADS_PER_SHOUP = {1: 16, 2: 60}
+MADS_PER_BARRETT = {1: 20, 2: 72}
+
+
+def brv(i: int, bits: int) -> int:
+    return int(format(i, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def residue_int(row, width: int) -> int:
+    """Python int of one residue (a uint64 scalar or a row of `width` words, low first)."""
+    if width == 1:
+        return int(row)
+    return sum(int(row[k]) << (64 * k) for k in range(width))
+
+
+def check_forward_samples(M, torch, dev, sh, plan, x_host, wl, bitrev, opts, n_poly=8, per_poly=8):
+    """The forward transform of the timed batched form, checked on its own: the batch's forward jobs
+    (the same kernel instantiation and work items as in the timed step) run once on a copy of the
+    input; the whole output must equal ntt_forward's, and n_poly x per_poly sampled outputs (plus
+    both ends of each sampled polynomial) must equal the oracle's O(N) evaluation of the sum
+    definition.  Returns (ok, samples checked, equal to the call form)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    N, batch, width, log2n = wl["N"], wl["batch"], wl["width"], wl["log2n"]
+    dv, dc = M.to_device(x_host, dev), M.to_device(x_host, dev)
+    jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, dv[b * N:(b + 1) * N], 1, N) for b in range(batch)]
+    fb = M.mq_batch_create(jobs, opts, stream=sh)
+    M.mq_batch_launch(fb, stream=sh)
+    status = M.mq_batch_status(fb)
+    M.ntt_forward(plan, dc, batch, N, stream=sh)
+    torch.cuda.synchronize()
+    got, call = M.to_host(dv), M.to_host(dc)
+    same_as_call = bool(np.array_equal(got, call))
+    del fb, dv, dc
+    shp = (batch, N) if width == 1 else (batch, N, width)
+    g, xs = got.reshape(shp), x_host.reshape(shp)
+    rng = np.random.default_rng(99)
+    polys = sorted(int(p) for p in rng.choice(batch, size=min(n_poly, batch), replace=False))
+    tasks = []
+    for p in polys:
+        for i in sorted({0, N - 1} | {int(v) for v in rng.choice(N, size=per_poly, replace=False)}):
+            k = brv(i, log2n) if bitrev else i
+            tasks.append((p, i, k))
+    O = oracle.default()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        want = list(ex.map(lambda t: O.ntt_point(xs[t[0]], log2n, wl["q"], wl["psi"], width, t[2]), tasks))
+    ok = status == 0 and all(residue_int(g[p, i], width) == w for (p, i, _), w in zip(tasks, want))
+    return bool(ok), len(tasks), same_as_call
 
 
 def parse():
@@ -60,11 +111,18 @@ def parse():
     p.add_argument("--no-polymul", action="store_true")
     p.add_argument("--no-wide", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=1.5)
+    p.add_argument("--serve-point-seconds", type=float, default=0.5,
+                   help="seconds of arrivals per point of the default line's short serving sweep")
+    p.add_argument("--no-serve", action="store_true", help="leave the short serving sweep out of the default line")
+    p.add_argument("--no-other-width", action="store_true",
+                   help="leave out the uniform batch at the other residue width (60-bit when --bits 124)")
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
     p.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: library default)")
     p.add_argument("--form", choices=["default", "split", "prefetch"], default="default",
                    help="persistent kernel form (default: the library's choice for the batch)")
     p.add_argument("--e2e-buffers", type=int, default=3, help="device buffers of the pipelined end-to-end loop (>= 2)")
+    p.add_argument("--int8-n", type=int, nargs="*", default=[4096, 8192, 16384],
+                   help="matrix sizes of the int8 / bf16 GEMM probe (--workload int8-probe)")
     return p.parse_args()
 
 
@@ -352,9 +410,12 @@ def run_gpu(args, rank, world):
     bfly = 2 * wl["butterflies_per_dir"]
     ms, value = aggregate(sum(t_batched) / len(t_batched), bfly, world, dev)
 
-    # correctness of what was timed: the round trip leaves the input unchanged
+    # correctness of what was timed: the round trip leaves the input unchanged, and the forward
+    # half, run alone by the same kernel, matches the oracle at sampled outputs
     batch_status = M.mq_batch_status(pbatch)
     ok_roundtrip = bool(np.array_equal(M.to_host(d), x_host)) and batch_status == 0
+    fwd_ok, fwd_n, fwd_call = check_forward_samples(M, torch, dev, sh, plan, x_host, wl, args.order == "bitrev",
+                                                    batch_opts(M, args))
 
     out = {"metric": METRIC, "value": value, "unit": "butterflies/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -365,7 +426,10 @@ def run_gpu(args, rank, world):
                               f"{pinfo['ctas']} CTAs)",
                       "l2": "L2 flushed between timed steps (2 x L2 write); working set "
                             f"{batch * N * 8 * width >> 20} MiB", "parallelism": f"replicas x{world}"},
-           "roundtrip_bit_exact": ok_roundtrip}
+           "roundtrip_bit_exact": ok_roundtrip, "forward_sampled_bit_exact": fwd_ok,
+           "forward_check": {"samples_vs_oracle": fwd_n, "whole_output_equals_call_form": fwd_call,
+                             "what": "the batch's forward jobs run alone on a copy of the input; sampled "
+                                     "outputs of 8 polynomials vs the oracle's sum definition"}}
 
     # gpu launches in the timed region: one persistent kernel per step (plus a counter memset and
     # a 4-byte status copy in the same graph)
@@ -395,7 +459,10 @@ def run_gpu(args, rank, world):
     ms_launch = statistics.median(t_roof)
     fw, iv = timed_dirs(max(3, args.steps))
     ms_f, ms_i = statistics.median(fw), statistics.median(iv)
-    mads_per_mul = 64 if width == 2 else 16   # 32-bit multiply instructions per Shoup product
+    # algorithmic 32-bit multiply instructions per Shoup product (a lo and a hi half per 32 x 32 limb
+    # product): 124-bit q, 30 limb products (10 for the quotient's high half, 10 each for the low
+    # halves of a w and qhat q) = 60; 60-bit q, lo(a w) 2 + hi(a w') 8 + lo(qhat q) ... = 16
+    mads_per_mul = MADS_PER_SHOUP[width]
     mad_f = wl["butterflies_per_dir"] * mads_per_mul
     mad_i = (wl["butterflies_per_dir"] + batch * N // 2) * mads_per_mul  # + N/2 folded N^-1 products
     alu_achieved = (mad_f + mad_i) / (ms_launch * 1e-3)
@@ -525,8 +592,14 @@ def run_gpu(args, rank, world):
     if not args.no_blas:
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
         out["small_ntt"] = bench_small_ntt(M, torch, dev, stream)
+    if not args.no_other_width:
+        out["c3_other_width"] = bench_c3_width(M, torch, dev, stream, flush, args, 60 if args.bits == 124 else 124)
     if not args.no_uneven:
-        out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args))
+        mix = uneven_mix(M, torch, dev)
+        out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args), mix)
+        if not args.no_serve:
+            out["serve"] = serve_sweep(M, torch, mix, args.serve_point_seconds)
+        del mix
     if width == 2:   # the two forms of the double-word product (Sec. 2.2, Eq. 8 and 9), multiply-bound
         r_s, _ = M.mq_probe_mulmod_rate(M.MQ_MUL_SCHOOLBOOK, 2000, q, stream=sh)
         r_k, _ = M.mq_probe_mulmod_rate(M.MQ_MUL_KARATSUBA, 2000, q, stream=sh)
@@ -542,6 +615,55 @@ def run_gpu(args, rank, world):
 
     out["clocks"] = clocks
     return out
+
+
+def bench_c3_width(M, torch, dev, stream, flush, args, bits):
+    """The uniform batch at another residue width (C3's second prime): per step, the batched
+    persistent form, one call per direction over the batch, and one call per polynomial and
+    direction; median event time with L2 flushed between steps; round trip and sampled forward
+    outputs checked."""
+    a2 = argparse.Namespace(**vars(args))
+    a2.bits = bits
+    wl = workload(a2)
+    from paper_2509_12494_gb300 import workload as W
+    N, batch, width = wl["N"], wl["batch"], wl["width"]
+    sh = stream.cuda_stream
+    flags = M.MQ_ORDER_BITREV if args.order == "bitrev" else M.MQ_ORDER_NATURAL
+    plan = M.ntt_plan_create(wl["log2n"], wl["q"], wl["psi"], width, flags, stream=sh)
+    x = W.gen_residues(batch * N, wl["q"], seed=12, width=width)
+    d = M.to_device(x, dev)
+    jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
+    jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
+    pb = M.mq_batch_create(jobs, batch_opts(M, args), stream=sh)
+
+    def batched():
+        M.mq_batch_launch(pb, stream=sh)
+
+    def call():
+        M.ntt_forward(plan, d, batch, N, stream=sh)
+        M.ntt_inverse(plan, d, batch, N, stream=sh)
+
+    def plain():
+        for b in range(batch):
+            M.ntt_forward(plan, d[b * N:(b + 1) * N], 1, N, stream=sh)
+        for b in range(batch):
+            M.ntt_inverse(plan, d[b * N:(b + 1) * N], 1, N, stream=sh)
+
+    reps = max(5, args.steps)
+    ms_b, _ = time_reps(torch, stream, batched, flush, reps, args.warmup)
+    ok = M.mq_batch_status(pb) == 0
+    ms_c, _ = time_reps(torch, stream, call, flush, reps, 2)
+    ms_p, _ = time_reps(torch, stream, plain, flush, max(3, reps // 3), 1)
+    torch.cuda.synchronize()
+    ok = ok and bool(np.array_equal(M.to_host(d), x))
+    fwd_ok, fwd_n, fwd_call = check_forward_samples(M, torch, dev, sh, plan, x, wl, args.order == "bitrev",
+                                                    batch_opts(M, args))
+    bfly = 2 * wl["butterflies_per_dir"]
+    del pb, d
+    return {"workload": workload_name(wl, a2), "q_bits": bits, "ms_batched": ms_b, "ms_call": ms_c, "ms_plain": ms_p,
+            "butterflies_per_s": bfly / (ms_b * 1e-3), "call_butterflies_per_s": bfly / (ms_c * 1e-3),
+            "plain_butterflies_per_s": bfly / (ms_p * 1e-3), "roundtrip_bit_exact": ok,
+            "forward_sampled_bit_exact": fwd_ok and fwd_call, "forward_samples": fwd_n}
 
 
 def bench_wide(M, torch, dev, sh, timed, args):
@@ -602,7 +724,7 @@ def bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mad
 
     ms_f = statistics.median(timed(step_fused, args.steps, args.warmup))
     ms_u = statistics.median(timed(step_unfused, args.steps, args.warmup))
-    barrett_mads = 80 if width == 2 else 20   # 32-bit multiply instructions per Barrett product
+    barrett_mads = MADS_PER_BARRETT[width]   # 32-bit multiply instructions per Barrett product
     mads = (3 * wl["butterflies_per_dir"] + batch * N // 2) * mads_per_mul + batch * N * barrett_mads
     del b, c, ta, tb
     return {"workload": f"{batch} products of degree-{N} polynomials mod (x^N + 1), {q.bit_length()}-bit q",
@@ -822,23 +944,30 @@ def batch_opts(M, args):
     return M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm, flags=form_flag)
 
 
-def bench_uneven(M, torch, dev, stream, flush, steps, opts=None):
-    mix = uneven_mix(M, torch, dev)
+def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None):
+    mix = mix or uneven_mix(M, torch, dev)
     sh = stream.cuda_stream
+    # every job's inputs as they were: NTT data (transformed in place) and axpy's y (updated in place)
+    saved_ntt = [t["d"].clone() for t in mix["ntt"]]
+    saved_y = [bj["c"].clone() if bj["op"] == "axpy" else None for bj in mix["blas"]]
     b = M.mq_batch_create(mix["jobs"], opts, stream=sh)
     info = M.mq_batch_info(b)
 
     def step_batch():
         M.mq_batch_launch(b, stream=sh)
 
-    def step_calls():
+    def calls(inverse=True):
         for t, bj in zip(mix["ntt"], mix["blas"]):
             M.ntt_forward(t["plan"], t["d"], 1, t["N"], stream=sh)
-            M.ntt_inverse(t["plan"], t["d"], 1, t["N"], stream=sh)
+            if inverse:
+                M.ntt_inverse(t["plan"], t["d"], 1, t["N"], stream=sh)
             if bj["op"] == "vmul":
                 M.mod_vmul(bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], stream=sh)
             else:
                 M.mod_axpy(bj["c"], bj["s"], bj["a"], bj["n"], bj["q"], bj["width"], stream=sh)
+
+    def step_calls():
+        calls(True)
 
     def timeit(step, k):
         with torch.cuda.stream(stream):
@@ -859,6 +988,52 @@ def bench_uneven(M, torch, dev, stream, flush, steps, opts=None):
     ms_b = timeit(step_batch, max(3, steps))
     status = M.mq_batch_status(b)
     ms_c = timeit(step_calls, max(2, steps // 2))
+
+    # checks of what was timed, job by job against the per-call path (itself pinned to the oracle
+    # by the tests): (1) the timed batch once on the saved inputs; (2) the forward transforms and
+    # the BLAS jobs as a batch of their own, so that the transforms' forward results are compared too
+    def restore():
+        for t, x0 in zip(mix["ntt"], saved_ntt):
+            t["d"].copy_(x0)
+        for bj, y0 in zip(mix["blas"], saved_y):
+            if y0 is not None:
+                bj["c"].copy_(y0)
+
+    def outputs():
+        return [t["d"].clone() for t in mix["ntt"]] + [bj["c"].clone() for bj in mix["blas"]]
+
+    def same(xs, ys):
+        return [bool(torch.equal(x, y)) for x, y in zip(xs, ys)]
+
+    with torch.cuda.stream(stream):
+        restore()
+        step_batch()
+        torch.cuda.synchronize()
+        st1 = M.mq_batch_status(b)
+        got = outputs()
+        restore()
+        calls(True)
+        torch.cuda.synchronize()
+        eq_all = same(got, outputs())
+        roundtrip = all(torch.equal(t["d"], x0) for t, x0 in zip(mix["ntt"], saved_ntt))
+        del got
+        restore()
+        fjobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, t["plan"], t["d"], 1, t["N"]) for t in mix["ntt"]]
+        for bj in mix["blas"]:
+            kind = M.MQ_JOB_VMUL if bj["op"] == "vmul" else M.MQ_JOB_AXPY
+            fjobs.append(M.blas_job(kind, bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], bj["s"]))
+        fb = M.mq_batch_create(fjobs, opts, stream=sh)
+        M.mq_batch_launch(fb, stream=sh)
+        st2 = M.mq_batch_status(fb)
+        got = outputs()
+        restore()
+        calls(False)
+        torch.cuda.synchronize()
+        eq_fwd = same(got, outputs())
+        del got, fb
+        restore()
+        torch.cuda.synchronize()
+    del saved_ntt, saved_y
     total = mix["butterflies"] + mix["blas_modmuls"]
     return {"workload": "uneven batch: 512 negacyclic NTTs (N uniform 2^12..2^17, own 60/124-bit prime each, "
                         "forward then inverse, bit-reversed order) interleaved with 512 vmul/axpy jobs "
@@ -868,7 +1043,47 @@ def bench_uneven(M, torch, dev, stream, flush, steps, opts=None):
             "items": info["items"], "per_call": {"modmul_per_s": total / (ms_c * 1e-3), "ms_per_step": ms_c,
                                                  "launches": 512 + sum(2 * (1 if t["N"] <= 4096 else 2) for t in mix["ntt"])},
             "batched_over_per_call": ms_c / ms_b, "butterflies": mix["butterflies"],
-            "blas_modmuls": mix["blas_modmuls"]}
+            "blas_modmuls": mix["blas_modmuls"],
+            "jobs_bit_exact_vs_per_call": bool(all(eq_all) and st1 == 0 and roundtrip),
+            "forward_jobs_bit_exact_vs_per_call": bool(all(eq_fwd) and st2 == 0),
+            "jobs_checked": len(eq_all) + len(eq_fwd)}
+
+
+def serve_sweep(M, torch, mix, seconds=0.5, fracs=(0.5, 1.0, 1.25)):
+    """A short serving sweep on the uneven mix's jobs (single forward transforms and BLAS requests,
+    Poisson arrivals): saturated throughput of both modes (everything submitted at once), then the
+    given fractions of the batched mode's saturation, for both modes."""
+    pool = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, t["plan"], t["d"], 1, t["N"]) for t in mix["ntt"]]
+    for bj in mix["blas"]:
+        kind = M.MQ_JOB_VMUL if bj["op"] == "vmul" else M.MQ_JOB_AXPY
+        pool.append(M.blas_job(kind, bj["c"], bj["a"], bj["b"], bj["n"], bj["q"], bj["width"], bj["s"]))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    pool = [pool[i] for i in rng.permutation(len(pool))]
+
+    def run(mode, rate, n_req, seed):
+        srv = M.mq_server_create(M.mq_server_cfg(mode=mode))
+        offered = M.mq_server_poisson(srv, pool, rate, n_req, seed)
+        M.mq_server_drain(srv, 300)
+        st = M.mq_server_stats(srv)
+        M.mq_server_destroy(srv)
+        return offered, st
+
+    modes = (("batched", M.MQ_SERVE_BATCHED), ("plain", M.MQ_SERVE_PLAIN))
+    sat = {name: run(mode, 0.0, 4 * len(pool), 1)[1]["jobs_per_s"] for name, mode in modes}
+    points = []
+    for name, mode in modes:
+        for frac in fracs:
+            rate = frac * sat["batched"]
+            n_req = int(max(200, min(rate * seconds, 200000)))
+            offered, st = run(mode, rate, n_req, 7)
+            points.append({"mode": name, "load": frac, "offered_per_s": offered, "jobs_per_s": st["jobs_per_s"],
+                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "modmul_per_s": st["modmul_per_s"],
+                           "failed": st["failed"]})
+    return {"workload": "Poisson arrivals of single requests from the uneven mix (forward NTT 2^12..2^17 or "
+                        "vmul/axpy 2^14..2^22, 60/124-bit), twiddles and operands resident, admission by free HBM; "
+                        f"load = fraction of the batched mode's saturated rate, {seconds} s of arrivals per point",
+            "saturated_jobs_per_s": sat, "points": points}
 
 
 # ----------------------------------------------------------------------------------- serving
@@ -992,29 +1207,84 @@ def run_int8_probe(args):
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    rates = {}
-    for n in (4096, 8192, 16384):
-        a = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
-        b = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+
+    def rate(n, dtype):
+        if dtype == torch.int8:
+            a = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+            b = torch.randint(-128, 127, (n, n), dtype=torch.int8, device=dev)
+            mm = torch._int_mm
+        else:
+            a = torch.randint(0, 256, (n, n), device=dev).to(dtype)
+            b = torch.randint(0, 256, (n, n), device=dev).to(dtype)
+            mm = torch.matmul
         for _ in range(3):
-            torch._int_mm(a, b)
+            mm(a, b)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 10
         e0.record()
         for _ in range(reps):
-            torch._int_mm(a, b)
+            mm(a, b)
         e1.record()
         torch.cuda.synchronize()
-        rates[n] = 2 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3)
-        del a, b
+        return 2 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3)
+
+    rates = {n: rate(n, torch.int8) for n in args.int8_n}
+    bf16 = {n: rate(n, torch.bfloat16) for n in args.int8_n}
     ops = max(rates.values())
     per_bfly = 2 * 16 * 16 * 16 * 16 / 32
     return {"metric": METRIC, "workload": "int8-probe", "int8_ops_per_s": ops,
-            "by_size": {str(k): v for k, v in rates.items()}, "limb_split_int8_ops_per_butterfly": per_bfly,
+            "by_size": {str(k): v for k, v in rates.items()},
+            "bf16_ops_per_s": max(bf16.values()), "bf16_by_size": {str(k): v for k, v in bf16.items()},
+            "limb_split_int8_ops_per_butterfly": per_bfly,
             "butterfly_bound_per_s": ops / per_bfly,
             "note": "upper bound from the tensor part alone; the reductions mod q of the wide accumulators "
                     "(CUDA cores) come on top"}
+
+
+def _r(v, nd=4):
+    """Round to nd significant digits (compact summary numbers)."""
+    if v is None or isinstance(v, bool):
+        return v
+    return float(f"{v:.{nd}g}")
+
+
+def tail_summary(out):
+    """Every config's headline numbers, compact, as the last key of the line (the part of the line a
+    reader sees first when only its end is kept).  Moves itself to the end."""
+    s = {"c3": {"bits": out["config"]["q_bits"], "ms_batched": _r(out["ms_per_step"]),
+                "ms_call": _r(out.get("batched_call", {}).get("ms_per_step")),
+                "ms_plain": _r(out.get("plain", {}).get("ms_per_step")),
+                "ms_e2e": _r(out.get("e2e", {}).get("ms_per_step")),
+                "fwd_exact": out.get("forward_sampled_bit_exact"), "rt_exact": out.get("roundtrip_bit_exact"),
+                "alu_frac": _r(out.get("roofline", {}).get("frac"), 3)}}
+    o = out.get("c3_other_width")
+    if o:
+        s["c3_other"] = {"bits": o["q_bits"], "ms_batched": _r(o["ms_batched"]), "ms_call": _r(o["ms_call"]),
+                         "ms_plain": _r(o["ms_plain"]), "exact": o["roundtrip_bit_exact"] and o["forward_sampled_bit_exact"]}
+    u = out.get("uneven")
+    if u:
+        s["c4"] = {"ms_batched": _r(u["ms_per_step"]), "ms_per_call": _r(u["per_call"]["ms_per_step"]),
+                   "modmul_per_s": _r(u["modmul_per_s"]), "exact": u["jobs_bit_exact_vs_per_call"] and
+                   u["forward_jobs_bit_exact_vs_per_call"], "autotuned": u.get("autotuned")}
+    v = out.get("serve")
+    if v:
+        s["c5"] = {"sat_jobs_per_s": {k: _r(x, 3) for k, x in v["saturated_jobs_per_s"].items()},
+                   "p50_p99_ms_jobs_per_s": {f"{p['mode']}@{p['load']}": [_r(p["p50_ms"], 3), _r(p["p99_ms"], 3),
+                                                                          _r(p["jobs_per_s"], 3)]
+                                             for p in v["points"]}}
+    b = out.get("blas")
+    if b:
+        s["c2_GBps"] = {k: _r(b[k].get("GB/s"), 3) for k in ("vadd_124", "vmul_124", "axpy_124", "vadd_60", "vmul_60")
+                        if k in b}
+        s["c2_GBps"]["vadd_124_2^20_dev"] = _r(b.get("vadd_124_n2^20", {}).get("GB/s_device"), 3)
+        s["c2_GBps"]["vmul_124_2^20_dev"] = _r(b.get("vmul_124_n2^20", {}).get("GB/s_device"), 3)
+    n = out.get("small_ntt")
+    if n:
+        s["c1_us"] = {"calls": _r(n["calls_us"], 3), "graph": _r(n["graph_us"], 3), "exact": n["roundtrip_bit_exact"]}
+    out.pop("summary", None)
+    out["summary"] = s
+    return out
 
 
 def main():
@@ -1046,6 +1316,8 @@ def main():
                                    "sample": f"{cores} of the {wl['batch']} transforms (half forward, half "
                                              f"inverse), one per host thread, {dt:.1f} s wall"}
     if out is not None and rank == 0:
+        if "ms_per_step" in out and "config" in out and args.impl != "reference":
+            tail_summary(out)
         print(json.dumps(out), flush=True)
     if world > 1 and args.impl != "reference":
         import torch.distributed as dist
