@@ -44,6 +44,14 @@ MADS_PER_SHOUP = {1: 16, 2: 60}
 MADS_PER_BARRETT = {1: 20, 2: 72}
 
 
+_T0 = time.time()
+
+
+def progress(msg: str):
+    """One line on stderr per phase of the run (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def brv(i: int, bits: int) -> int:
     return int(format(i, f"0{bits}b")[::-1], 2) if bits else 0
 
@@ -403,6 +411,7 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in fw], [a.elapsed_time(b) for a, b in iv]
 
+    progress("timing the batched form")
     nvml = NvmlClocks(dev)
     with ClockSampler(dev.index) as clk:
         t_batched = timed(step_batched, args.steps, args.warmup, nvml)
@@ -414,6 +423,7 @@ def run_gpu(args, rank, world):
     # half, run alone by the same kernel, matches the oracle at sampled outputs
     batch_status = M.mq_batch_status(pbatch)
     ok_roundtrip = bool(np.array_equal(M.to_host(d), x_host)) and batch_status == 0
+    progress("checking the forward half against the oracle")
     fwd_ok, fwd_n, fwd_call = check_forward_samples(M, torch, dev, sh, plan, x_host, wl, args.order == "bitrev",
                                                     batch_opts(M, args))
 
@@ -439,6 +449,7 @@ def run_gpu(args, rank, world):
     if rank != 0:
         return None
 
+    progress("call form and plain calls")
     # the same work as one call per direction over the whole batch
     t_call = timed(step_call, max(3, args.steps), 1)
     ms_call = sum(t_call) / len(t_call)
@@ -545,6 +556,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / steps
 
+    progress("end to end")
     e2e_run(args.warmup)
     n_e2e = max(E2E_STEPS, args.steps)
     ms_e2e = statistics.median(e2e_run(n_e2e) for _ in range(E2E_JOBS))
@@ -590,14 +602,18 @@ def run_gpu(args, rank, world):
     del dbuf[1:], pbs[1:]
 
     if not args.no_blas:
+        progress("BLAS")
         out["blas"] = bench_blas(M, torch, dev, stream, flush)
         out["small_ntt"] = bench_small_ntt(M, torch, dev, stream)
     if not args.no_other_width:
+        progress("uniform batch at the other width")
         out["c3_other_width"] = bench_c3_width(M, torch, dev, stream, flush, args, 60 if args.bits == 124 else 124)
     if not args.no_uneven:
+        progress("uneven batch")
         mix = uneven_mix(M, torch, dev)
         out["uneven"] = bench_uneven(M, torch, dev, stream, flush, args.steps, batch_opts(M, args), mix)
         if not args.no_serve:
+            progress("serving sweep")
             out["serve"] = serve_sweep(M, torch, mix, args.serve_point_seconds)
         del mix
     if width == 2:   # the two forms of the double-word product (Sec. 2.2, Eq. 8 and 9), multiply-bound
@@ -608,8 +624,10 @@ def run_gpu(args, rank, world):
                                 "schoolbook_mulmod_per_s": r_s, "karatsuba_mulmod_per_s": r_k,
                                 "karatsuba_over_schoolbook": r_k / r_s}
     if not args.no_wide:
+        progress("wide residues")
         out["wide"] = bench_wide(M, torch, dev, sh, timed, args)
     if not args.no_polymul:
+        progress("polynomial product")
         out["polymul"] = bench_polymul(M, torch, dev, sh, timed, plan, d, batch, N, q, width, wl, mads_per_mul,
                                        alu_peak, args)
 
@@ -944,12 +962,33 @@ def batch_opts(M, args):
     return M.mq_batch_opts(lag=args.lag, ctas_per_sm=args.ctas_per_sm, flags=form_flag)
 
 
-def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None):
+def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None, tune=True):
     mix = mix or uneven_mix(M, torch, dev)
     sh = stream.cuda_stream
     # every job's inputs as they were: NTT data (transformed in place) and axpy's y (updated in place)
     saved_ntt = [t["d"].clone() for t in mix["ntt"]]
     saved_y = [bj["c"].clone() if bj["op"] == "axpy" else None for bj in mix["blas"]]
+    tuned = None
+    if opts is None and tune:
+        # the library's autotuner on this batch shape (it runs the batch, so the inputs are restored
+        # below); its choice goes through a cache file as a user's would
+        import tempfile
+        t0 = time.perf_counter()
+        with tempfile.TemporaryDirectory() as tdir:
+            progress("autotuning the uneven batch")
+        opts = M.mq_autotune_batch(mix["jobs"], os.path.join(tdir, "tune.json"), stream=sh)
+        progress("autotuned")
+        form = ("calls" if opts.flags & M.MQ_BATCH_FORM_CALLS else "split" if opts.flags & M.MQ_BATCH_FORM_SPLIT
+                else "prefetch")
+        tuned = {"form": form, "ctas_per_sm": opts.ctas_per_sm, "lag": opts.lag, "blas_chunk": opts.blas_chunk,
+                 "split_shift": opts.split_shift, "tune_s": time.perf_counter() - t0}
+        with torch.cuda.stream(stream):
+            for t, x0 in zip(mix["ntt"], saved_ntt):
+                t["d"].copy_(x0)
+            for bj, y0 in zip(mix["blas"], saved_y):
+                if y0 is not None:
+                    bj["c"].copy_(y0)
+        torch.cuda.synchronize()
     b = M.mq_batch_create(mix["jobs"], opts, stream=sh)
     info = M.mq_batch_info(b)
 
@@ -987,7 +1026,9 @@ def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None):
 
     ms_b = timeit(step_batch, max(3, steps))
     status = M.mq_batch_status(b)
+    progress(f"uneven batch timed ({ms_b:.2f} ms, status {status}); per-call path")
     ms_c = timeit(step_calls, max(2, steps // 2))
+    progress("uneven batch: per-job checks")
 
     # checks of what was timed, job by job against the per-call path (itself pinned to the oracle
     # by the tests): (1) the timed batch once on the saved inputs; (2) the forward transforms and
@@ -1044,6 +1085,7 @@ def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None):
                                                  "launches": 512 + sum(2 * (1 if t["N"] <= 4096 else 2) for t in mix["ntt"])},
             "batched_over_per_call": ms_c / ms_b, "butterflies": mix["butterflies"],
             "blas_modmuls": mix["blas_modmuls"],
+            "autotuned": tuned,
             "jobs_bit_exact_vs_per_call": bool(all(eq_all) and st1 == 0 and roundtrip),
             "forward_jobs_bit_exact_vs_per_call": bool(all(eq_fwd) and st2 == 0),
             "jobs_checked": len(eq_all) + len(eq_fwd)}
@@ -1071,18 +1113,24 @@ def serve_sweep(M, torch, mix, seconds=0.5, fracs=(0.5, 1.0, 1.25)):
 
     modes = (("batched", M.MQ_SERVE_BATCHED), ("plain", M.MQ_SERVE_PLAIN))
     sat = {name: run(mode, 0.0, 4 * len(pool), 1)[1]["jobs_per_s"] for name, mode in modes}
+    progress(f"saturation {sat}")
+    # the batched mode at fractions of its saturated rate; the plain mode at fractions of its own, and
+    # at half the batched mode's saturated rate (far beyond what it sustains)
+    plan = [("batched", M.MQ_SERVE_BATCHED, "batched", f) for f in fracs]
+    plan += [("plain", M.MQ_SERVE_PLAIN, "plain", f) for f in (0.5, 1.0)]
+    plan += [("plain", M.MQ_SERVE_PLAIN, "batched", 0.5)]
     points = []
-    for name, mode in modes:
-        for frac in fracs:
-            rate = frac * sat["batched"]
-            n_req = int(max(200, min(rate * seconds, 200000)))
-            offered, st = run(mode, rate, n_req, 7)
-            points.append({"mode": name, "load": frac, "offered_per_s": offered, "jobs_per_s": st["jobs_per_s"],
-                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "modmul_per_s": st["modmul_per_s"],
-                           "failed": st["failed"]})
+    for name, mode, base, frac in plan:
+        rate = frac * sat[base]
+        n_req = int(max(200, min(rate * seconds, 200000)))
+        offered, st = run(mode, rate, n_req, 7)
+        progress(f"serving point {name} at {frac} x {base}: p50 {st['p50_ms']:.3f} ms")
+        points.append({"mode": name, "load": frac, "of": base, "offered_per_s": offered, "jobs_per_s": st["jobs_per_s"],
+                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "modmul_per_s": st["modmul_per_s"],
+                       "failed": st["failed"]})
     return {"workload": "Poisson arrivals of single requests from the uneven mix (forward NTT 2^12..2^17 or "
                         "vmul/axpy 2^14..2^22, 60/124-bit), twiddles and operands resident, admission by free HBM; "
-                        f"load = fraction of the batched mode's saturated rate, {seconds} s of arrivals per point",
+                        f"load = fraction of the saturated rate of mode `of`, {seconds} s of arrivals per point",
             "saturated_jobs_per_s": sat, "points": points}
 
 
@@ -1266,12 +1314,13 @@ def tail_summary(out):
     if u:
         s["c4"] = {"ms_batched": _r(u["ms_per_step"]), "ms_per_call": _r(u["per_call"]["ms_per_step"]),
                    "modmul_per_s": _r(u["modmul_per_s"]), "exact": u["jobs_bit_exact_vs_per_call"] and
-                   u["forward_jobs_bit_exact_vs_per_call"], "autotuned": u.get("autotuned")}
+                   u["forward_jobs_bit_exact_vs_per_call"],
+                   "tuned": ({k: v for k, v in u["autotuned"].items() if k != "tune_s"} if u.get("autotuned") else None)}
     v = out.get("serve")
     if v:
         s["c5"] = {"sat_jobs_per_s": {k: _r(x, 3) for k, x in v["saturated_jobs_per_s"].items()},
-                   "p50_p99_ms_jobs_per_s": {f"{p['mode']}@{p['load']}": [_r(p["p50_ms"], 3), _r(p["p99_ms"], 3),
-                                                                          _r(p["jobs_per_s"], 3)]
+                   "p50_p99_ms_jobs_per_s": {f"{p['mode']}@{p['load']}x{p['of'][0]}": [_r(p["p50_ms"], 3), _r(p["p99_ms"], 3),
+                                                                                        _r(p["jobs_per_s"], 3)]
                                              for p in v["points"]}}
     b = out.get("blas")
     if b:
@@ -1309,6 +1358,7 @@ def main():
     else:
         out = run_gpu(args, rank, world)
         if out is not None and not args.no_cpu_baseline:
+            progress("oracle on the host cores")
             wl = workload(args)
             cores = os.cpu_count() or 1
             v, dt, cores = oracle_sample(args, wl, cores)

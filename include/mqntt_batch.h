@@ -62,6 +62,10 @@ typedef struct mq_batch_opts {
     unsigned blas_chunk;   /* residues per BLAS work item (0: 16384); a multiple of 2048 */
     double wait_timeout_s; /* limit of every device-side wait (0: 2 s) */
     unsigned flags;        /* MQ_BATCH_* */
+    int split_shift;       /* stage fusion of transforms above 2^11: the first pass (columns of the
+                              forward, undone last by the inverse) fuses floor(log2 N / 2) + split_shift
+                              stages, the second the rest; clamped so that both passes hold 6 to 11
+                              stages (0: the even split).  Results do not depend on it. */
 } mq_batch_opts;
 
 #define MQ_BATCH_NO_GRAPH 1u       /* launch the kernel directly instead of replaying a graph */
@@ -73,6 +77,11 @@ typedef struct mq_batch_opts {
 #define MQ_BATCH_FORM_SPLIT 4u    /* warp-specialised: two producer warps stage items for eight compute warps */
 #define MQ_BATCH_FORM_PREFETCH 8u /* every warp computes; a CTA starts its next item's copies before the
                                      current transform when that item's dependencies are already met */
+#define MQ_BATCH_FORM_CALLS 16u   /* no persistent kernel: the graph holds each job's own kernels (the
+                                     transform passes and BLAS kernels of the per-call entry points), in job
+                                     order.  The default for a batch with fewer work items than the GPU has
+                                     SMs and no checked job, where a persistent grid would mostly idle;
+                                     refused (MQ_ERR_ARG) for a batch with checked jobs */
 
 typedef struct mq_batch mq_batch;
 
@@ -105,17 +114,20 @@ int mq_batch_launch(mq_batch *b, void *stream);
  */
 int mq_batch_status(mq_batch *b);
 
-/* Work items, persistent CTAs and items of each kind, for reports (any pointer may be NULL). */
+/* Work items, persistent CTAs (0 for the calls form) and items of each kind, for reports (any pointer
+   may be NULL). */
 int mq_batch_info(const mq_batch *b, size_t *items, unsigned *ctas, size_t *ntt_items, size_t *blas_items);
 
 /* Free a batch (synchronises with the device first).  NULL is accepted. */
 int mq_batch_destroy(mq_batch *b);
 
 /*
- * Autotuner: time candidate options (kernel form, CTAs per SM, pipeline lag, BLAS chunk) on this batch shape
- * with a few launches each, write the fastest to *best and, if cache_path is non-NULL, record it
- * in that JSON cache under a key made of the device name and the batch shape.  The jobs' buffers
- * are overwritten (the timing runs the batch).  Errors: those of mq_batch_create.
+ * Autotuner: time candidate options on this batch shape with a few launches each -- the persistent
+ * forms x CTAs per SM x pipeline lag x BLAS chunk, then, around the fastest, the stage fusion of
+ * two-pass transforms (split_shift -1, +1) and the calls form -- write the fastest to *best and, if
+ * cache_path is non-NULL, record it in that JSON cache under a key made of the device name and the
+ * batch shape (each job's kind, size, width, order and dependency).  The jobs' buffers are
+ * overwritten (the timing runs the batch).  Errors: those of mq_batch_create.
  */
 int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts *best, const char *cache_path, void *stream);
 

@@ -81,6 +81,7 @@ struct mq_batch {
     cudaEvent_t done = nullptr, staged = nullptr;
     int *h_status = nullptr;
     bool launched = false;
+    bool calls = false;                // MQ_BATCH_FORM_CALLS: the graph holds the jobs' own kernels
     CheckRec *dcheck = nullptr;        // operands of the jobs that carry MQ_CHECK_INPUTS (device table)
     unsigned n_check = 0;
     unsigned long long check_max = 0;  // residues of the largest checked operand
@@ -150,7 +151,13 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
         d.width = p->width;
         d.inv = inv;
         d.twopass = logN > LMAX;
-        const int L1 = d.twopass ? logN / 2 : 0, L2 = logN - L1;
+        int L1 = 0;
+        if (d.twopass) {  // stage fusion: the even split moved by split_shift, both passes within LMIN..LMAX
+            L1 = logN / 2 + o.split_shift;
+            L1 = std::max(L1, std::max(LMIN, logN - LMAX));
+            L1 = std::min(L1, std::min(LMAX, logN - LMIN));
+        }
+        const int L2 = logN - L1;
         for (int k = 0; k < 2; ++k) {
             PassArgs &a = d.pa[k];
             a.tw = inv ? p->tw_inv : p->tw_fwd;
@@ -497,13 +504,51 @@ static void destroy_batch(mq_batch *b) {
     delete b;
 }
 
+// The calls form of one job: the kernels the per-call entry points launch for it (transform passes
+// with the batch's pass split and staging, or the BLAS kernel), on `s`.
+static cudaError_t launch_job_calls(const JobDev &d, cudaStream_t s) {
+    if (d.kind == JK_NTT) {
+        cudaError_t e = launch_ntt_pass(d.width, d.L[0], d.inv != 0, d.pa[0], s);
+        if (e == cudaSuccess && d.twopass) e = launch_ntt_pass(d.width, d.L[1], d.inv != 0, d.pa[1], s);
+        return e;
+    }
+    return launch_blas(d.width, d.op, d.ba, s);
+}
+
 static int enqueue_run(mq_batch *b, cudaStream_t s) {
+    if (b->calls) {  // every job's kernels in job order: an earlier job always finishes first
+        cudaError_t e = cudaMemsetAsync(b->dctrs, 0, b->n_ctrs * sizeof(unsigned), s);
+        for (size_t i = 0; i < b->hjobs.size() && e == cudaSuccess; ++i) e = launch_job_calls(b->hjobs[i], s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+        return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "batch launch (calls form)");
+    }
     cudaError_t e = launch_persistent(b->variant, b->form, b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
                                       (unsigned)b->hjobs.size(), b->limit_ns, b->grid, b->smem, s, b->dcheck, b->n_check,
                                       b->check_max);
     if (e != cudaSuccess) return mq_cuda_fail(e, "persistent kernel launch");
     e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return mq_cuda_fail(e, "status copy");
+    return MQ_OK;
+}
+
+// Capture one launch (enqueue_run) on the batch's stream into a graph, instantiate and upload it.
+// A graph captured before is destroyed first (the calls form captures its jobs' pointers, so an
+// update re-captures).
+static int capture_graph(mq_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return mq_cuda_fail(e, "graph capture");
+    int rc = enqueue_run(b, b->cs);
+    cudaError_t e2 = cudaStreamEndCapture(b->cs, &b->graph);
+    if (rc) return rc;
+    if (e2 != cudaSuccess) return mq_cuda_fail(e2, "graph capture");
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return mq_cuda_fail(e, "graph instantiate");
+    // upload now, so that the first launch does not pay for it on the caller's stream
+    if ((e = cudaGraphUpload(b->exec, b->cs)) != cudaSuccess || (e = cudaStreamSynchronize(b->cs)) != cudaSuccess)
+        return mq_cuda_fail(e, "graph upload");
     return MQ_OK;
 }
 
@@ -590,32 +635,28 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
             b->n_check = (unsigned)recs.size();
         }
     }
+    {
+        // the calls form: asked for, or the default when a persistent grid would mostly idle
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        const unsigned forms = b->opts.flags & (MQ_BATCH_FORM_SPLIT | MQ_BATCH_FORM_PREFETCH | MQ_BATCH_FORM_CALLS);
+        if ((forms & MQ_BATCH_FORM_CALLS) && b->n_check) {
+            destroy_batch(b);
+            return mq_fail(MQ_ERR_ARG, "the calls form does not run the input check of checked jobs");
+        }
+        b->calls = (forms & MQ_BATCH_FORM_CALLS) || (!forms && !b->n_check && b->n_items < (size_t)sms);
+        // a persistent grid of no more CTAs than there are items
+        b->grid = (unsigned)std::min<size_t>(b->grid, std::max<size_t>(1, b->n_items));
+    }
     if ((e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess) {
         destroy_batch(b);
         return mq_cuda_fail(e, "batch stream/events");
     }
-    if (!(b->opts.flags & MQ_BATCH_NO_GRAPH)) {
-        if ((e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-            destroy_batch(b);
-            return mq_cuda_fail(e, "graph capture");
-        }
-        rc = enqueue_run(b, b->cs);
-        cudaError_t e2 = cudaStreamEndCapture(b->cs, &b->graph);
-        if (rc || e2 != cudaSuccess) {
-            destroy_batch(b);
-            return rc ? rc : mq_cuda_fail(e2, "graph capture");
-        }
-        if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
-            destroy_batch(b);
-            return mq_cuda_fail(e, "graph instantiate");
-        }
-        // upload now, so that the first launch does not pay for it on the caller's stream
-        if ((e = cudaGraphUpload(b->exec, b->cs)) != cudaSuccess || (e = cudaStreamSynchronize(b->cs)) != cudaSuccess) {
-            destroy_batch(b);
-            return mq_cuda_fail(e, "graph upload");
-        }
+    if (!(b->opts.flags & MQ_BATCH_NO_GRAPH) && (rc = capture_graph(b))) {
+        destroy_batch(b);
+        return rc;
     }
     *out = b;
     return MQ_OK;
@@ -646,6 +687,11 @@ extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, vo
             return mq_cuda_fail(e, "input check table upload");
     }
     for (size_t i = 0; i < njobs; ++i) b->shape[i] = jobs[i];
+    if (b->calls && b->exec) {  // the graph holds the old pointers: capture it again once it is idle
+        if (b->launched && (e = cudaEventSynchronize(b->done)) != cudaSuccess) return mq_cuda_fail(e, "batch wait");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return mq_cuda_fail(e, "job table upload");
+        return capture_graph(b);
+    }
     return MQ_OK;
 }
 
@@ -680,7 +726,7 @@ extern "C" int mq_batch_status(mq_batch *b) {
 extern "C" int mq_batch_info(const mq_batch *b, size_t *items, unsigned *ctas, size_t *ntt_items, size_t *blas_items) {
     if (!b) return mq_fail(MQ_ERR_ARG, "batch is NULL");
     if (items) *items = b->n_items;
-    if (ctas) *ctas = b->grid;
+    if (ctas) *ctas = b->calls ? 0u : b->grid;
     if (ntt_items) *ntt_items = b->ntt_items;
     if (blas_items) *blas_items = b->blas_items;
     return MQ_OK;
@@ -739,20 +785,24 @@ static std::string read_file(const char *path) {
     return s;
 }
 
-// The cache is a JSON object of "key": {"ctas_per_sm": c, "lag": l, "blas_chunk": b, "ms": t}.
+// The cache is a JSON object of "key": {"ctas_per_sm": c, "lag": l, "blas_chunk": b, "form": f, "split": s,
+// "ms": t} with f = 0 (warp-specialised), 1 (prefetching) or 2 (calls).
 static bool cache_get(const char *path, const std::string &key, mq_batch_opts &o) {
     std::string s = read_file(path);
     size_t at = s.find("\"" + key + "\"");
     if (at == std::string::npos) return false;
     unsigned c = 0, l = 0, bc = 0, form = 1;
+    int split = 0;
     const int got = sscanf(s.c_str() + at + key.size() + 2,
-                           " : {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %u", &c, &l, &bc, &form);
+                           " : {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %u, \"split\": %d", &c,
+                           &l, &bc, &form, &split);
     if (got < 3) return false;
     o.ctas_per_sm = c;
     o.lag = l;
     o.blas_chunk = bc;
-    o.flags = (o.flags & ~(MQ_BATCH_FORM_SPLIT | MQ_BATCH_FORM_PREFETCH)) |
-              (form ? MQ_BATCH_FORM_PREFETCH : MQ_BATCH_FORM_SPLIT);
+    o.split_shift = split;
+    o.flags = (o.flags & ~(MQ_BATCH_FORM_SPLIT | MQ_BATCH_FORM_PREFETCH | MQ_BATCH_FORM_CALLS)) |
+              (form == 2 ? MQ_BATCH_FORM_CALLS : form ? MQ_BATCH_FORM_PREFETCH : MQ_BATCH_FORM_SPLIT);
     return true;
 }
 
@@ -769,8 +819,10 @@ static void cache_put(const char *path, const std::string &key, const mq_batch_o
         pos = end;
     }
     char buf[512];
-    snprintf(buf, sizeof buf, "\"%s\": {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %d, \"ms\": %.4f}",
-             key.c_str(), o.ctas_per_sm, o.lag, o.blas_chunk, (o.flags & MQ_BATCH_FORM_SPLIT) ? 0 : 1, ms);
+    const int form = (o.flags & MQ_BATCH_FORM_CALLS) ? 2 : (o.flags & MQ_BATCH_FORM_SPLIT) ? 0 : 1;
+    snprintf(buf, sizeof buf,
+             "\"%s\": {\"ctas_per_sm\": %u, \"lag\": %u, \"blas_chunk\": %u, \"form\": %d, \"split\": %d, \"ms\": %.4f}",
+             key.c_str(), o.ctas_per_sm, o.lag, o.blas_chunk, form, o.split_shift, ms);
     entries.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "wb");
@@ -791,10 +843,13 @@ static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o) {
 extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts *best, const char *cache_path, void *stream) {
     if (!jobs || !njobs || !best) return mq_fail(MQ_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    bool has_blas = false, has_deps = false;
+    bool has_blas = false, has_deps = false, has_twopass = false, has_check = false;
     for (size_t i = 0; i < njobs; ++i) {
-        has_blas |= !is_ntt(jobs[i].kind);
-        has_deps |= jobs[i].after >= 0 || (is_ntt(jobs[i].kind) && jobs[i].plan && jobs[i].plan->log2n > LMAX);
+        const bool ntt = is_ntt(jobs[i].kind);
+        has_blas |= !ntt;
+        has_twopass |= ntt && jobs[i].plan && jobs[i].plan->log2n > LMAX;
+        has_deps |= jobs[i].after >= 0 || (ntt && jobs[i].plan && jobs[i].plan->log2n > LMAX);
+        has_check |= ntt ? (jobs[i].plan && (jobs[i].plan->flags & MQ_CHECK_INPUTS)) : (((unsigned)jobs[i].width & MQ_CHECK_INPUTS) != 0);
     }
     const unsigned forms[] = {MQ_BATCH_FORM_PREFETCH, MQ_BATCH_FORM_SPLIT};
     const unsigned ctas[] = {1, 2, 3};
@@ -805,7 +860,32 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
+    // mean event time of 5 launches after 2 warm-ups; keeps the fastest in bo / best_ms
+    auto trial = [&](const mq_batch_opts &o) -> int {
+        mq_batch *b = nullptr;
+        int rc = mq_batch_create(&b, jobs, njobs, &o, stream);
+        if (rc) return rc;
+        float ms = 0, sum = 0;
+        for (int r = 0; r < 2; ++r) mq_batch_launch(b, stream);
+        for (int r = 0; r < 5; ++r) {
+            cudaEventRecord(t0, s);
+            mq_batch_launch(b, stream);
+            cudaEventRecord(t1, s);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(&ms, t0, t1);
+            sum += ms;
+        }
+        rc = mq_batch_status(b);
+        mq_batch_destroy(b);
+        if (rc) return rc;
+        if (sum / 5 < best_ms) {
+            best_ms = sum / 5;
+            bo = o;
+        }
+        return MQ_OK;
+    };
     int rc = MQ_OK;
+    // 1. the persistent forms x CTAs per SM x lag x BLAS chunk
     for (unsigned fm : forms) {
         unsigned last_grid = 0;
         for (unsigned c : ctas) {
@@ -824,29 +904,24 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
                     o.lag = l;
                     o.blas_chunk = ch;
                     o.flags = fm;
-                    mq_batch *b = nullptr;
-                    rc = mq_batch_create(&b, jobs, njobs, &o, stream);
-                    if (rc) goto done;
-                    float ms = 0, sum = 0;
-                    for (int r = 0; r < 2; ++r) mq_batch_launch(b, stream);  // warm-up
-                    for (int r = 0; r < 5; ++r) {
-                        cudaEventRecord(t0, s);
-                        mq_batch_launch(b, stream);
-                        cudaEventRecord(t1, s);
-                        cudaEventSynchronize(t1);
-                        cudaEventElapsedTime(&ms, t0, t1);
-                        sum += ms;
-                    }
-                    rc = mq_batch_status(b);
-                    mq_batch_destroy(b);
-                    if (rc) goto done;
-                    if (sum / 5 < best_ms) {
-                        best_ms = sum / 5;
-                        bo = o;
-                    }
+                    if ((rc = trial(o))) goto done;
                 }
             }
         }
+    }
+    // 2. around the fastest: the stage fusion of two-pass transforms, then the calls form
+    if (has_twopass) {
+        const mq_batch_opts base = bo;
+        for (int sh : {-1, 1}) {
+            mq_batch_opts o = base;
+            o.split_shift = sh;
+            if ((rc = trial(o))) goto done;
+        }
+    }
+    if (!has_check) {
+        mq_batch_opts o = bo;
+        o.flags = (o.flags & ~(MQ_BATCH_FORM_SPLIT | MQ_BATCH_FORM_PREFETCH)) | MQ_BATCH_FORM_CALLS;
+        if ((rc = trial(o))) goto done;
     }
     *best = bo;
     apply_defaults(*best);

@@ -29,6 +29,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+// Add one to a completion counter with release semantics at GPU scope: the writes that precede it
+// (this thread's, and cumulatively those ordered before it by a barrier) are visible to any thread
+// that acquires the counter and sees the increment.  No return value, so the thread does not wait
+// for the addition itself.
+__device__ __forceinline__ void red_release_add(unsigned *p) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
 __device__ __forceinline__ int ld_status(const unsigned *p) {
     return (int)*(const volatile unsigned *)p;
 }
@@ -316,7 +324,10 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     __shared__ BlasArgs s_ba[2];
     __shared__ __align__(16) ItemDev s_rec[3];  // records of items k, k + 1, k + 2 (slot k % 3)
     __shared__ unsigned s_idx[3];               // their indices (n_items: none)
-    __shared__ int s_ready;
+    // whether item k + 1's dependency was met when item k started, by the parity of k: thread 0 writes
+    // item k + 1's flag before the first barrier of item k + 1, while slower threads may still be
+    // reading item k's at the end of item k, so the two must not share a word
+    __shared__ int s_ready[2];
     const int tid = threadIdx.x;
     unsigned *status = ctrs + 1;
     (void)njobs;
@@ -349,6 +360,12 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     };
 
     unsigned pend = 0;  // thread 0: index of the item after the two whose records are in flight
+    unsigned pend_bump = 0, pend_job = 0;  // thread 0: completion counters not yet incremented (0: none)
+    auto signal_pending = [&]() {
+        if (pend_bump) red_release_add(ctrs + pend_bump);
+        if (pend_job) red_release_add(ctrs + pend_job);
+        pend_bump = pend_job = 0;
+    };
     if (tid == 0) {
         const unsigned i0 = atomicAdd(ctrs, 1u), i1 = atomicAdd(ctrs, 1u);
         pend = atomicAdd(ctrs, 1u);
@@ -371,16 +388,17 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
             asm volatile("cp.async.wait_all;" ::: "memory");  // the record of item k + 1
             int ready = 1;
             if (s_idx[r1] < n_items && s_rec[r1].dep) ready = ld_acquire(ctrs + s_rec[r1].dep) >= s_rec[r1].target;
-            s_ready = ready;
+            s_ready[b] = ready;
         }
-        __syncthreads();  // s_ready, and the record of item k + 1
-        bool early = s_idx[r1] < n_items && s_ready;
+        __syncthreads();  // s_ready[b], and the record of item k + 1
+        bool early = s_idx[r1] < n_items && s_ready[b];
         if (early) stage(b ^ 1, s_rec[r1]);
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (early) asm volatile("cp.async.wait_group 1;" ::: "memory");
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();  // every thread's copies of the current item (and its arguments) landed
-        if (tid == 0) {   // the record of item k + 2 and the index of item k + 3
+        if (tid == 0) {   // the previous item's completion, the record of item k + 2, the index of item k + 3
+            signal_pending();
             const unsigned i2 = pend < n_items ? pend : n_items;
             s_idx[r2] = i2;
             if (i2 < n_items) copy_record(&s_rec[r2], items + i2);
@@ -409,24 +427,31 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
             else if (WM & 2) run_blas<2>(J->op, ba, begin, end, tid);
             ntt_detail::tile_sync<BAR_COMPUTE, BT>();
         }
-        // every thread's stores precede the barrier that ends the item; thread 0's release makes
-        // them visible (cumulatively) to whoever acquires the counters
+        // every thread's stores precede the barrier that ends the item; thread 0's release additions
+        // make them visible (cumulatively) to whoever acquires the counters.  When the next item is
+        // already staged, the additions wait until that item's copies have landed (below, after the
+        // second barrier of the next iteration), so that their latency overlaps the next transform
+        // instead of holding every warp at the next barrier; before any wait of this CTA they are
+        // made at once, so no wait can depend on an addition this CTA has not made yet.
         if (tid == 0) {
-            __threadfence();
-            if (item.bump) atomicAdd(ctrs + item.bump, 1u);
-            atomicAdd(ctrs + 2 + item.job, 1u);
+            pend_bump = item.bump;
+            pend_job = 2 + item.job;
         }
         // re-read from shared memory rather than keep registers live across the transform
-        // (s_ready and s_idx[r1] change only at the next item's start or in the late path below)
-        early = s_ready;
+        // (s_ready[b] changes only at item k + 2's start, s_idx[r1] only in the late path below)
+        early = s_ready[b];
         if (s_idx[(k + 1) % 3] < n_items && !early) {  // the next item was not ready: wait for it now, then stage it
             const int q1 = (k + 1) % 3;
-            if (tid == 0) wait_for(q1);
+            if (tid == 0) {
+                signal_pending();
+                wait_for(q1);
+            }
             __syncthreads();
             if (s_idx[q1] < n_items) stage((k & 1) ^ 1, s_rec[q1]);
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
     }
+    if (tid == 0) signal_pending();  // the last item's completion
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 

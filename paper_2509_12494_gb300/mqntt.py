@@ -244,7 +244,7 @@ def mq_version() -> str:
 
 MQ_JOB_NTT_FORWARD, MQ_JOB_NTT_INVERSE, MQ_JOB_VADD, MQ_JOB_VSUB, MQ_JOB_VMUL, MQ_JOB_AXPY = 1, 2, 3, 4, 5, 6
 MQ_BATCH_NO_GRAPH, MQ_BATCH_TEST_DROP_ITEM = 1, 2
-MQ_BATCH_FORM_SPLIT, MQ_BATCH_FORM_PREFETCH = 4, 8
+MQ_BATCH_FORM_SPLIT, MQ_BATCH_FORM_PREFETCH, MQ_BATCH_FORM_CALLS = 4, 8, 16
 
 
 class mq_job(ctypes.Structure):
@@ -255,7 +255,7 @@ class mq_job(ctypes.Structure):
 
 class mq_batch_opts(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_uint), ("lag", ctypes.c_uint), ("blas_chunk", ctypes.c_uint),
-                ("wait_timeout_s", ctypes.c_double), ("flags", ctypes.c_uint)]
+                ("wait_timeout_s", ctypes.c_double), ("flags", ctypes.c_uint), ("split_shift", ctypes.c_int)]
 
 
 def ntt_job(kind: int, plan: Plan, data, batch: int = 1, stride: int = 0, after: int = -1) -> mq_job:

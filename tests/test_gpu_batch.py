@@ -94,12 +94,14 @@ class BlasCase:
         return oracle.blas(self.OOPS[self.op], self.a, self.b, self.q, self.width, s=self.s)
 
 
-FORMS = ["split", "prefetch"]
+FORMS = ["split", "prefetch", "calls"]
+PERSISTENT = ["split", "prefetch"]
 
 
 def _opts(M, form, **kw):
-    """Batch options selecting a kernel form (both must give identical results)."""
-    flags = kw.pop("flags", 0) | {"split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[form]
+    """Batch options selecting a form (all must give identical results)."""
+    flags = kw.pop("flags", 0) | {"split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH,
+                                  "calls": M.MQ_BATCH_FORM_CALLS}[form]
     return M.mq_batch_opts(flags=flags, **kw)
 
 
@@ -243,7 +245,7 @@ def test_no_graph_mode_matches(mq):
     assert np.array_equal(mq.to_host(c.d), want)
 
 
-@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("form", PERSISTENT)
 def test_bounded_wait_reports_timeout_and_device_stays_usable(mq, form):
     """Fault injection: one first-pass item is left out, so the second pass of that polynomial
     waits for a counter nothing will complete.  The wait gives up after the limit, the batch
@@ -267,16 +269,16 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(mq, form):
     assert np.array_equal(mq.to_host(c2.d), want)
 
 
-@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("form", PERSISTENT)
 def test_instantiation_follows_batch_contents(mq, form):
     """Split form: 64-bit transforms alone run three persistent CTAs per SM, any batch with 128-bit
     residues or BLAS two.  Prefetch form: four for 64-bit transforms alone, three otherwise.  An
-    explicit ctas_per_sm is clamped to what the instantiation holds.  Each batch's results equal the
-    per-call path's."""
+    explicit ctas_per_sm is clamped to what the instantiation holds, and the grid to the batch's
+    work items.  Each batch's results equal the per-call path's."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    c60 = NttCase(mq, 14, 60, 2, 0, False, 61)
-    c124 = NttCase(mq, 14, 124, 2, 0, True, 62)
+    c60 = NttCase(mq, 14, 60, 48, 0, False, 61)    # 768 items: more than any grid holds
+    c124 = NttCase(mq, 14, 124, 48, 0, True, 62)
     bl = BlasCase(mq, "vmul", 70001, 60, 63)
     two = 2 if form == "split" else 3
     alone60 = 3 if form == "split" else 4
@@ -288,13 +290,41 @@ def test_instantiation_follows_batch_contents(mq, form):
             if isinstance(j, NttCase):
                 j.d.copy_(mq.to_device(j.x).view_as(j.d))
         b = _run(mq, [j.job() for j in jobs], _opts(mq, form, **kw))
-        assert mq.mq_batch_info(b)["ctas"] == sms * ctas
+        assert mq.mq_batch_info(b)["ctas"] == min(sms * ctas, mq.mq_batch_info(b)["items"])
         for j, w in zip(jobs, wants):
             if w is not None:
                 assert np.array_equal(mq.to_host(j.d), w)
             else:
                 assert np.array_equal(mq.to_host(j.dc), j.expect())
         mq.mq_batch_destroy(b)
+
+
+def test_small_batch_takes_the_calls_form(mq):
+    """A forward and inverse of one N = 1024 polynomial (two work items): by default the graph holds
+    the jobs' own kernels (no persistent grid); equal to the per-call path and to the persistent
+    form; a batch with a checked job refuses the calls form and takes a persistent one by default."""
+    q = W.gen_prime(124, 11, 5)
+    psi = W.gen_root(q, 10, 5)
+    plan = mq.ntt_plan_create(10, q, psi, 2, 0)
+    x = W.gen_residues(1024, q, 5, width=2)
+    d = mq.to_device(x)
+    fwd = NttCase(mq, 10, 124, 1, 0, False, 5, plan=plan)
+    jobs = [mq.ntt_job(mq.MQ_JOB_NTT_FORWARD, plan, d, 1, 1024), mq.ntt_job(mq.MQ_JOB_NTT_INVERSE, plan, d, 1, 1024, 0)]
+    b = _run(mq, jobs)
+    assert mq.mq_batch_info(b)["ctas"] == 0
+    assert np.array_equal(mq.to_host(d), x)
+    # forward alone: equal to the per-call path, in both forms
+    for opts in (None, _opts(mq, "prefetch")):
+        fwd.d.copy_(mq.to_device(fwd.x))
+        bf = _run(mq, [fwd.job()], opts)
+        assert (mq.mq_batch_info(bf)["ctas"] == 0) == (opts is None)
+        assert np.array_equal(mq.to_host(fwd.d), fwd.per_call())
+    checked = mq.ntt_plan_create(10, q, psi, 2, mq.MQ_CHECK_INPUTS)
+    cj = [mq.ntt_job(mq.MQ_JOB_NTT_FORWARD, checked, d, 1, 1024)]
+    with pytest.raises(mq.MqError) as e:
+        mq.mq_batch_create(cj, _opts(mq, "calls"))
+    assert e.value.code == mq.MQ_ERR_ARG
+    assert mq.mq_batch_info(_run(mq, cj))["ctas"] > 0
 
 
 def test_rejects_bad_jobs(mq):
@@ -307,18 +337,56 @@ def test_rejects_bad_jobs(mq):
     assert e.value.code == mq.MQ_ERR_SIZE
 
 
+def _restore(cases, bl):
+    for c in cases:
+        c.d.copy_(c.M.to_device(c.x).view_as(c.d))
+    bl.db.copy_(bl.M.to_device(bl.b).view_as(bl.db))
+
+
+def _check_results(mq, cases, bl):
+    for c in cases:
+        assert np.array_equal(mq.to_host(c.d), c.per_call()), (c.log2n, c.inverse)
+    assert np.array_equal(mq.to_host(bl.dc), bl.expect())
+
+
+@pytest.mark.parametrize("split_shift", [-1, 0, 1, 3])
+@pytest.mark.parametrize("form", FORMS)
+def test_every_tuner_axis_is_bit_exact(mq, form, split_shift):
+    """Every choice the autotuner can make -- form, stage fusion of two-pass transforms (split_shift,
+    clamped to passes of 6..11 stages), CTAs per SM, lag, BLAS chunk -- gives the per-call path's
+    results: two-pass transforms of odd and even log N in both orders and directions, with BLAS."""
+    cases = [NttCase(mq, 13, 124, 4, 2, False, 70), NttCase(mq, 15, 60, 3, 0, True, 71),
+             NttCase(mq, 16, 124, 2, 0, False, 72), NttCase(mq, 17, 60, 1, 2, True, 73)]
+    bl = BlasCase(mq, "axpy", 100000, 60, 74)
+    jobs = [c.job() for c in cases] + [bl.job()]
+    for kw in ({}, {"ctas_per_sm": 1, "lag": 1, "blas_chunk": 8192}):
+        _restore(cases, bl)
+        b = _run(mq, jobs, _opts(mq, form, split_shift=split_shift, **kw))
+        _check_results(mq, cases, bl)
+        mq.mq_batch_destroy(b)
+
+
 def test_autotuner_writes_cache_and_create_uses_it(mq, tmp_path, monkeypatch):
-    cases = [NttCase(mq, 13, 124, 4, 2, False, 50 + i) for i in range(2)]
+    """The tuner's choice is recorded in the cache under the batch shape; mq_batch_create without
+    options takes it from there, and the tuned batch's results equal the per-call path's."""
+    import torch
+    cases = [NttCase(mq, 13, 124, 4, 2, False, 50 + i) for i in range(2)] + [NttCase(mq, 15, 60, 3, 0, True, 53)]
     bl = BlasCase(mq, "axpy", 100000, 60, 52)
     jobs = [c.job() for c in cases] + [bl.job()]
     cache = str(tmp_path / "tune.json")
     best = mq.mq_autotune_batch(jobs, cache)
     assert best.ctas_per_sm in (1, 2, 3) and best.lag >= 1 and best.blas_chunk % 2048 == 0
-    assert bin(best.flags & (mq.MQ_BATCH_FORM_SPLIT | mq.MQ_BATCH_FORM_PREFETCH)).count("1") == 1
+    forms = best.flags & (mq.MQ_BATCH_FORM_SPLIT | mq.MQ_BATCH_FORM_PREFETCH | mq.MQ_BATCH_FORM_CALLS)
+    assert bin(forms).count("1") == 1 and best.split_shift in (-1, 0, 1)
     text = open(cache).read()
-    assert '"ctas_per_sm"' in text and '"form"' in text and '"ms"' in text
+    assert all(k in text for k in ('"ctas_per_sm"', '"form"', '"split"', '"ms"'))
     monkeypatch.setenv("MQNTT_TUNE_CACHE", cache)
-    b = mq.mq_batch_create(jobs)
-    import torch
+    _restore(cases, bl)
+    b = _run(mq, jobs)
+    info = mq.mq_batch_info(b)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert mq.mq_batch_info(b)["ctas"] == sms * best.ctas_per_sm
+    if forms == mq.MQ_BATCH_FORM_CALLS:
+        assert info["ctas"] == 0
+    else:
+        assert info["ctas"] == min(sms * best.ctas_per_sm, info["items"])
+    _check_results(mq, cases, bl)
