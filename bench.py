@@ -122,6 +122,9 @@ def parse():
     p.add_argument("--serve-point-seconds", type=float, default=0.5,
                    help="seconds of arrivals per point of the default line's short serving sweep")
     p.add_argument("--no-serve", action="store_true", help="leave the short serving sweep out of the default line")
+    p.add_argument("--tune", action="store_true",
+                   help="autotune the uniform batch before timing it (its choice on the GB300 equals the library's "
+                        "defaults: prefetching form, 3 CTAs per SM, lag 8, even split); the uneven batch is always tuned")
     p.add_argument("--no-other-width", action="store_true",
                    help="leave out the uniform batch at the other residue width (60-bit when --bits 124)")
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")
@@ -354,6 +357,19 @@ def run_gpu(args, rank, world):
     jobs = [M.ntt_job(M.MQ_JOB_NTT_FORWARD, plan, d[b * N:(b + 1) * N], 1, N) for b in range(batch)]
     jobs += [M.ntt_job(M.MQ_JOB_NTT_INVERSE, plan, d[b * N:(b + 1) * N], 1, N, after=b) for b in range(batch)]
     opts = batch_opts(M, args)
+    tuned = None
+    if opts is None and args.tune:
+        # the library's autotuner on this batch shape, through a cache file as a user would run it
+        # (it runs the batch, so the input is restored afterwards)
+        import tempfile
+        progress("autotuning the uniform batch")
+        t0 = time.perf_counter()
+        with tempfile.TemporaryDirectory() as tdir:
+            opts = M.mq_autotune_batch(jobs, os.path.join(tdir, "tune.json"), stream=sh)
+        tuned = describe_opts(M, opts)
+        tuned["tune_s"] = time.perf_counter() - t0
+        d.copy_(M.to_device(x_host, dev))
+        torch.cuda.synchronize()
     pbatch = M.mq_batch_create(jobs, opts, stream=sh)
     pinfo = M.mq_batch_info(pbatch)
 
@@ -434,6 +450,7 @@ def run_gpu(args, rank, world):
                       "q_bits": args.bits, "order": args.order,
                       "form": f"batched persistent kernel in a CUDA graph ({pinfo['items']} work items, "
                               f"{pinfo['ctas']} CTAs)",
+                      "batch_options": tuned or "library defaults",
                       "l2": "L2 flushed between timed steps (2 x L2 write); working set "
                             f"{batch * N * 8 * width >> 20} MiB", "parallelism": f"replicas x{world}"},
            "roundtrip_bit_exact": ok_roundtrip, "forward_sampled_bit_exact": fwd_ok,
@@ -954,6 +971,14 @@ def uneven_mix(M, torch, dev, seed=4):
     return dict(ntt=ntt, blas=blas, jobs=jobs, butterflies=bfly, blas_modmuls=mm)
 
 
+def describe_opts(M, o):
+    """The options a batch was built with, for the report."""
+    form = ("calls" if o.flags & M.MQ_BATCH_FORM_CALLS else "split" if o.flags & M.MQ_BATCH_FORM_SPLIT
+            else "prefetch")
+    return {"form": form, "ctas_per_sm": o.ctas_per_sm, "lag": o.lag, "blas_chunk": o.blas_chunk,
+            "split_shift": o.split_shift}
+
+
 def batch_opts(M, args):
     """Options of the persistent batches from the command line (None: the library's defaults)."""
     form_flag = {"default": 0, "split": M.MQ_BATCH_FORM_SPLIT, "prefetch": M.MQ_BATCH_FORM_PREFETCH}[args.form]
@@ -978,10 +1003,8 @@ def bench_uneven(M, torch, dev, stream, flush, steps, opts=None, mix=None, tune=
             progress("autotuning the uneven batch")
         opts = M.mq_autotune_batch(mix["jobs"], os.path.join(tdir, "tune.json"), stream=sh)
         progress("autotuned")
-        form = ("calls" if opts.flags & M.MQ_BATCH_FORM_CALLS else "split" if opts.flags & M.MQ_BATCH_FORM_SPLIT
-                else "prefetch")
-        tuned = {"form": form, "ctas_per_sm": opts.ctas_per_sm, "lag": opts.lag, "blas_chunk": opts.blas_chunk,
-                 "split_shift": opts.split_shift, "tune_s": time.perf_counter() - t0}
+        tuned = describe_opts(M, opts)
+        tuned["tune_s"] = time.perf_counter() - t0
         with torch.cuda.stream(stream):
             for t, x0 in zip(mix["ntt"], saved_ntt):
                 t["d"].copy_(x0)

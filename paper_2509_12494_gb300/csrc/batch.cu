@@ -340,7 +340,8 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
             k.chain = chain[i];
             k.key = chain_pos[k.chain] + (unsigned long long)k.stage * lag_items;
             k.it.job = (unsigned)i;
-            k.it.pass = pass;
+            k.it.pass = (unsigned short)pass;
+            k.it.meta = (unsigned short)item_meta(d.kind == JK_BLAS, d.width, d.inv != 0, d.kind == JK_NTT ? d.L[pass] : 0);
             k.it.poly = poly;
             k.it.dep = k.it.target = k.it.bump = 0;  // resolved once every job's item count is known
             k.it.first = first;
@@ -852,7 +853,7 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
         has_check |= ntt ? (jobs[i].plan && (jobs[i].plan->flags & MQ_CHECK_INPUTS)) : (((unsigned)jobs[i].width & MQ_CHECK_INPUTS) != 0);
     }
     const unsigned forms[] = {MQ_BATCH_FORM_PREFETCH, MQ_BATCH_FORM_SPLIT};
-    const unsigned ctas[] = {1, 2, 3};
+    const unsigned ctas[] = {1, 2, 3, 4};  // beyond what an instantiation holds, the grid repeats and is skipped
     const unsigned lags[] = {1, 2, 4, 8};
     const unsigned chunks[] = {8192, 16384, 65536};
     double best_ms = 1e30;

@@ -41,7 +41,9 @@ struct JobDev {
 // finished first-pass items per polynomial of two-pass transforms.
 struct ItemDev {
     unsigned job;
-    unsigned pass;
+    unsigned short pass;
+    unsigned short meta;  // what the kernel needs to pick its code path without reading the job
+                          // descriptor: ITEM_BLAS | ITEM_W128 | ITEM_INV | (tile log size << 4)
     unsigned poly;
     unsigned dep;     // counter this item waits for, 0: none
     unsigned target;  // value the dependency counter must reach
@@ -49,6 +51,10 @@ struct ItemDev {
     unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
 };
 static_assert(sizeof(ItemDev) == 32, "work items are copied as two 16-byte halves");
+constexpr unsigned ITEM_BLAS = 1, ITEM_W128 = 2, ITEM_INV = 4;
+__host__ __device__ constexpr unsigned item_meta(bool blas, int width, bool inv, int L) {
+    return (blas ? ITEM_BLAS : 0u) | (width == 2 ? ITEM_W128 : 0u) | (inv ? ITEM_INV : 0u) | ((unsigned)L << 4);
+}
 
 // Host-side expansion of a job list into the device tables of one launch.
 struct BatchTables {

@@ -335,15 +335,17 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     // all threads: copy the item's arguments and start staging its tiles into buffer b
     auto stage = [&](int b, const ItemDev &item) {
         const JobDev *J = jobs + item.job;
-        if (!BL || J->kind == JK_NTT) {
-            const unsigned *src = reinterpret_cast<const unsigned *>(&J->pa[item.pass]);
+        const unsigned m = item.meta;  // kind, width and tile size without a read of the job descriptor
+        if (!BL || !(m & ITEM_BLAS)) {
+            const PassArgs &pa = J->pa[item.pass];
+            const unsigned *src = reinterpret_cast<const unsigned *>(&pa);
             unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
             for (int w = tid; w < (int)(sizeof(PassArgs) / 4); w += BT) dst[w] = src[w];
             unsigned char *buf = smem_raw + b * buf_bytes;
-            if ((WM & 1) && (!(WM & 2) || J->width == 1))
-                stage_tiles<1, BT, true>(J->L[item.pass], J->pa[item.pass], item.first, buf, tid);
+            if ((WM & 1) && (!(WM & 2) || !(m & ITEM_W128)))
+                stage_tiles<1, BT, true>((int)(m >> 4), pa, item.first, buf, tid);
             else if (WM & 2)
-                stage_tiles<2, BT>(J->L[item.pass], J->pa[item.pass], item.first, buf, tid);
+                stage_tiles<2, BT>((int)(m >> 4), pa, item.first, buf, tid);
         } else {
             const unsigned *src = reinterpret_cast<const unsigned *>(&J->ba);
             unsigned *dst = reinterpret_cast<unsigned *>(&s_ba[b]);
@@ -407,19 +409,19 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
         }
 
         const ItemDev &item = s_rec[r];
-        const JobDev *J = jobs + item.job;
-        const int kind = J->kind;
+        const unsigned m = item.meta;
         unsigned char *buf = smem_raw + b * buf_bytes;
-        if (!BL || kind == JK_NTT) {
-            const int L = J->L[item.pass];
-            if ((WM & 1) && (!(WM & 2) || J->width == 1)) {
-                if (J->inv) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
+        if (!BL || !(m & ITEM_BLAS)) {
+            const int L = (int)(m >> 4);
+            if ((WM & 1) && (!(WM & 2) || !(m & ITEM_W128))) {
+                if (m & ITEM_INV) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
                 else compute_store<1, false>(L, s_pa[b], item.first, buf, tid);
             } else if (WM & 2) {
-                if (J->inv) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
+                if (m & ITEM_INV) compute_store<2, true>(L, s_pa[b], item.first, buf, tid);
                 else compute_store<2, false>(L, s_pa[b], item.first, buf, tid);
             }
         } else if (BL) {
+            const JobDev *J = jobs + item.job;
             const BlasArgs &ba = s_ba[b];
             const unsigned long long begin = item.first * J->chunk;
             const unsigned long long end = begin + J->chunk < ba.n ? begin + J->chunk : ba.n;
