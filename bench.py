@@ -1304,11 +1304,16 @@ def run_int8_probe(args):
     bf16 = {n: rate(n, torch.bfloat16) for n in args.int8_n}
     ops = max(rates.values())
     per_bfly = 2 * 16 * 16 * 16 * 16 / 32
+    # the exact bf16 formulation: K = 16 inputs x 16 limbs of 8 bits (partial sums below 2^24, exact
+    # in fp32), a Toeplitz-expanded operand of 31 limb shifts per column, 16 outputs per 32 butterflies
+    bf16_per_bfly = 2 * 16 * 256 * 31 / 32
     return {"metric": METRIC, "workload": "int8-probe", "int8_ops_per_s": ops,
             "by_size": {str(k): v for k, v in rates.items()},
             "bf16_ops_per_s": max(bf16.values()), "bf16_by_size": {str(k): v for k, v in bf16.items()},
             "limb_split_int8_ops_per_butterfly": per_bfly,
             "butterfly_bound_per_s": ops / per_bfly,
+            "bf16_limb_split_flops_per_butterfly": bf16_per_bfly,
+            "bf16_butterfly_bound_per_s": max(bf16.values()) / bf16_per_bfly,
             "note": "upper bound from the tensor part alone; the reductions mod q of the wide accumulators "
                     "(CUDA cores) come on top"}
 

@@ -517,10 +517,10 @@ static cudaError_t launch_job_calls(const JobDev &d, cudaStream_t s) {
 }
 
 static int enqueue_run(mq_batch *b, cudaStream_t s) {
-    if (b->calls) {  // every job's kernels in job order: an earlier job always finishes first
-        cudaError_t e = cudaMemsetAsync(b->dctrs, 0, b->n_ctrs * sizeof(unsigned), s);
+    if (b->calls) {  // every job's kernels in job order: an earlier job always finishes first.  Nothing
+                     // waits on the device, so there are no counters to reset and the status stays MQ_OK.
+        cudaError_t e = cudaSuccess;
         for (size_t i = 0; i < b->hjobs.size() && e == cudaSuccess; ++i) e = launch_job_calls(b->hjobs[i], s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_status, b->dctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
         return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "batch launch (calls form)");
     }
     cudaError_t e = launch_persistent(b->variant, b->form, b->djobs, b->ditems, (unsigned)b->n_items, b->dctrs, b->n_ctrs,
