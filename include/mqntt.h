@@ -53,6 +53,7 @@ extern "C" {
 #define MQ_ERR_TIMEOUT (-8)  /* a bounded device-side wait gave up */
 #define MQ_ERR_RANGE (-9)    /* an input residue was not canonical (checked modes only) */
 #define MQ_ERR_STATE (-10)   /* object in the wrong state for the call */
+#define MQ_ERR_CANCELLED (-11) /* a served request was cancelled before it ran (mqntt_serve.h) */
 
 /* residue widths */
 #define MQ_W64 1  /* uint64_t residues, q < 2^60 */

@@ -3,8 +3,13 @@
  *
  * Clients submit single jobs (an NTT of a plan, or one BLAS operation) over device buffers they own
  * and keep resident; plans (twiddle tables) stay resident too.  A server thread admits requests by
- * device memory -- each in-flight request holds its operand bytes, plus staging for natural-order
- * transforms above 2^12, against a budget -- and forms batches of whatever has arrived whenever an
+ * device memory, twice over: each in-flight request holds its operand bytes, plus staging for
+ * natural-order transforms above 2^12, against a budget; and the staging, which the server
+ * allocates itself, is taken only while the device has it (cudaMemGetInfo's free memory plus what
+ * the library's pool holds unused, less `reserve_bytes`).  A staging allocation that fails all the
+ * same defers the batch's requests to the head of the queue, where they wait for requests in flight
+ * to free memory; with nothing in flight the first of them that needs staging fails with
+ * MQ_ERR_OOM after the wait limit.  The server forms batches of whatever has arrived whenever an
  * in-flight slot is free, launching each batch as one persistent kernel (mqntt_batch.h) on the
  * slot's own stream.  Requests that arrive while other batches run join the next batch, so their
  * work overlaps on the device with the batches already running.  Every result is the same as the
@@ -34,6 +39,7 @@ typedef struct mq_server_cfg {
     double linger_us;         /* with a slot free, wait up to this long for more arrivals (0: none) */
     double wait_timeout_s;    /* limit of the device-side waits (0: 2 s) */
     int mode;                 /* MQ_SERVE_BATCHED or MQ_SERVE_PLAIN */
+    size_t reserve_bytes;     /* device memory staging allocations leave free (0: 256 MiB) */
 } mq_server_cfg;
 
 typedef struct mq_stats {
@@ -45,6 +51,8 @@ typedef struct mq_stats {
     double modmul_per_s;                    /* modular products (butterflies, vmul and axpy elements) / span */
     double mean_batch_jobs;
     size_t peak_inflight_bytes;
+    uint64_t cancelled;                     /* requests cancelled while queued (not in the latencies) */
+    uint64_t deferred;                      /* requests sent back to the queue by a failed staging allocation */
 } mq_stats;
 
 typedef struct mq_server mq_server;
@@ -56,9 +64,25 @@ int mq_server_create(mq_server **out, const mq_server_cfg *cfg);
  * Submit one job (mq_job of mqntt_batch.h; `after` must be -1).  Returns at once with a ticket.
  * The job's buffers (and plan) must stay valid and untouched until the ticket completes.  A job
  * larger than the whole budget is rejected with MQ_ERR_SIZE; other argument errors are reported
- * here (MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_MODULUS, MQ_ERR_RANGE).
+ * here (MQ_ERR_ARG, MQ_ERR_ALIGN, MQ_ERR_MODULUS, MQ_ERR_RANGE).  A ticket finishes with MQ_OK,
+ * MQ_ERR_CANCELLED (mq_cancel), MQ_ERR_OOM (no staging memory with nothing in flight, after the wait
+ * limit), MQ_ERR_TIMEOUT (a device-side wait of its batch gave up) or the error of its launch.
  */
 int mq_submit(mq_server *s, const mq_job *job, uint64_t *ticket);
+
+/*
+ * Cancel a request that is still queued: it finishes at once with status MQ_ERR_CANCELLED, and its
+ * buffers are not touched.  MQ_ERR_STATE if it already joined a launched batch or finished (it then
+ * runs to completion as usual); MQ_ERR_ARG for an unknown ticket.
+ */
+int mq_cancel(mq_server *s, uint64_t ticket);
+
+/*
+ * Fault injection for tests: the server's next `n` staging allocations report failure as if the
+ * device were out of memory (0 clears it).  Nothing on the device is touched; the requests concerned
+ * are deferred as a real failure would defer them.
+ */
+int mq_server_inject_alloc_failures(mq_server *s, unsigned n);
 
 /* Non-blocking: *done = 1 once the ticket finished; *status = its status (MQ_OK or an error). */
 int mq_poll(mq_server *s, uint64_t ticket, int *done, int *status);

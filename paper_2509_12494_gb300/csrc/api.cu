@@ -118,6 +118,20 @@ int mq_pool_free(void *p, cudaStream_t s) {
     return e == cudaSuccess ? MQ_OK : mq_cuda_fail(e, "cudaFreeAsync");
 }
 
+// bytes the current device's pool holds without having handed them out (0 before its first use):
+// memory a new allocation can take besides what the device reports free
+size_t mq_pool_idle_bytes() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_ok[dev]) return 0;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(g_pool[dev], cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(g_pool[dev], cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+        return 0;
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 // ------------------------------------------------------------------------------------------------
 // plans
 // ------------------------------------------------------------------------------------------------

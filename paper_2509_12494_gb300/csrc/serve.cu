@@ -8,6 +8,13 @@
 // transforms above 2^12 get their staging from the library's stream-ordered pool on that stream.
 // The plain mode runs each request as its own per-call launch instead, on one stream, with one
 // callback per request: the same arrivals through the per-call path, for comparison.
+//
+// Staging is the memory the server itself allocates, so its admission asks the device: a request
+// that needs staging joins a batch only while cudaMemGetInfo's free memory, plus what the pool
+// holds unused, less a reserve, covers the batch's staging.  An allocation that fails all the same
+// (another process took the memory, or an injected failure) puts the batch's requests back at the
+// head of the queue, in order; they wait for requests in flight to free memory, and with nothing
+// in flight the first of them that needs staging fails with MQ_ERR_OOM after the wait limit.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -29,6 +36,7 @@ int mq_fail(int code, const char *fmt, ...);
 int mq_cuda_fail(cudaError_t e, const char *where);
 int mq_pool_alloc(void **p, size_t bytes, cudaStream_t s);
 int mq_pool_free(void *p, cudaStream_t s);
+size_t mq_pool_idle_bytes();
 
 using namespace mq::batch_detail;
 
@@ -96,14 +104,58 @@ struct Server {
     std::atomic<uint64_t> plain_outstanding{0};
     std::thread th;
     bool stop = false;
+    std::atomic<unsigned> inject_fail{0};  // staging allocations still to fail (fault injection)
+    uint64_t short_since = 0;              // since when staging has been short with nothing in flight
     // statistics since the last reset
     std::vector<double> lat_ms;
-    uint64_t completed = 0, failed = 0, batches = 0, batch_jobs = 0;
+    uint64_t completed = 0, failed = 0, batches = 0, batch_jobs = 0, cancelled = 0, deferred = 0;
     uint64_t t_first = 0, t_last = 0;
     double bfly = 0, mm = 0;
     int thread_error = MQ_OK;
 
     Ticket &ticket(uint64_t id) { return tickets[id - 1]; }
+
+    // Device memory the next staging allocations may take: what the device reports free plus what
+    // the library's pool holds unused, less the configured reserve.
+    size_t device_available() const {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const size_t a = fr + mq_pool_idle_bytes();
+        return a > cfg.reserve_bytes ? a - cfg.reserve_bytes : 0;
+    }
+
+    // A staging allocation on behalf of a request: true when an injected failure is due.
+    bool take_injected_failure() {
+        unsigned n = inject_fail.load();
+        while (n && !inject_fail.compare_exchange_weak(n, n - 1)) {
+        }
+        return n != 0;
+    }
+
+    // Staging could not be had for the queue's first request that needs some.  With requests in
+    // flight it waits for them to finish and free theirs; with none, the memory is held outside
+    // the server, and once that has lasted the server's wait limit that request fails with
+    // MQ_ERR_OOM (and so does each next one short of memory, at once, until a batch launches or
+    // the queue empties).  Under mu; true if a request was failed (the caller may try again).
+    bool expire_short_head(bool in_flight) {
+        auto it = std::find_if(pending.begin(), pending.end(),
+                               [&](uint64_t id) { return job_scratch_bytes(ticket(id).job) != 0; });
+        if (in_flight || it == pending.end()) {
+            short_since = 0;
+            return false;
+        }
+        const uint64_t t = now_ns();
+        if (!short_since) short_since = t;
+        if ((double)(t - short_since) < cfg.wait_timeout_s * 1e9) return false;
+        const uint64_t id = *it;
+        pending.erase(it);
+        inflight += ticket(id).bytes;  // finish() releases what admission would have held
+        finish(id, MQ_ERR_OOM, t);
+        return true;
+    }
 
     void finish(uint64_t id, int status, uint64_t t_done) {  // under mu
         Ticket &t = ticket(id);
@@ -174,6 +226,7 @@ int grow(Slot *sl, size_t njobs, size_t nitems, size_t nctrs) {
         if (sl->hjobs) cudaFreeHost(sl->hjobs);
         sl->djobs = nullptr;
         sl->hjobs = nullptr;
+        sl->cap_jobs = 0;
         if ((e = cudaMalloc(&sl->djobs, cap * sizeof(JobDev))) != cudaSuccess ||
             (e = cudaMallocHost(&sl->hjobs, cap * sizeof(JobDev))) != cudaSuccess)
             return mq_fail(MQ_ERR_OOM, "server tables do not fit");
@@ -185,6 +238,7 @@ int grow(Slot *sl, size_t njobs, size_t nitems, size_t nctrs) {
         if (sl->hitems) cudaFreeHost(sl->hitems);
         sl->ditems = nullptr;
         sl->hitems = nullptr;
+        sl->cap_items = 0;
         if ((e = cudaMalloc(&sl->ditems, cap * sizeof(ItemDev))) != cudaSuccess ||
             (e = cudaMallocHost(&sl->hitems, cap * sizeof(ItemDev))) != cudaSuccess)
             return mq_fail(MQ_ERR_OOM, "server tables do not fit");
@@ -194,6 +248,7 @@ int grow(Slot *sl, size_t njobs, size_t nitems, size_t nctrs) {
         size_t cap = std::max(nctrs, 2 * sl->cap_ctrs);
         if (sl->dctrs) cudaFree(sl->dctrs);
         sl->dctrs = nullptr;
+        sl->cap_ctrs = 0;
         if ((e = cudaMalloc(&sl->dctrs, cap * sizeof(unsigned))) != cudaSuccess)
             return mq_fail(MQ_ERR_OOM, "server counters do not fit");
         sl->cap_ctrs = cap;
@@ -208,7 +263,10 @@ int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
     int rc = MQ_OK;
     for (size_t i = 0; i < n && !rc; ++i) {
         size_t b = job_scratch_bytes(jobs[i]);
-        if (b) rc = mq_pool_alloc(&scratch[i], b, sl->stream);
+        if (b && s->take_injected_failure())
+            rc = mq_fail(MQ_ERR_OOM, "injected staging allocation failure (%zu bytes)", b);
+        else if (b)
+            rc = mq_pool_alloc(&scratch[i], b, sl->stream);
     }
     BatchTables t;
     unsigned grid = 0;
@@ -244,6 +302,8 @@ int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
 int run_plain(Server *s, uint64_t id) {
     const mq_job &j = s->ticket(id).job;
     void *st = (void *)s->plain_stream;
+    if (job_scratch_bytes(j) && s->take_injected_failure())
+        return mq_fail(MQ_ERR_OOM, "injected staging allocation failure (%zu bytes)", job_scratch_bytes(j));
     int rc;
     switch (j.kind) {
     case MQ_JOB_NTT_FORWARD: rc = ntt_forward(j.plan, j.data, j.batch ? j.batch : 1, j.stride, st); break;
@@ -284,11 +344,27 @@ void server_loop(Server *s) {
         if (s->stop && s->pending.empty() && !any_busy && s->plain_outstanding.load() == 0) break;
 
         // dispatch
+        if (s->pending.empty()) s->short_since = 0;
         if (s->cfg.mode == MQ_SERVE_PLAIN) {
+            size_t avail = 0;  // staging the device can still give in this pass (asked once per pass)
+            bool asked = false;
             while (!s->pending.empty()) {
                 const uint64_t id = s->pending.front();
                 Ticket &t = s->ticket(id);
-                if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes && s->plain_outstanding.load() > 0) break;
+                const bool others = s->plain_outstanding.load() > 0;
+                if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes && others) break;
+                const size_t sb = job_scratch_bytes(t.job);
+                if (sb) {
+                    if (!asked) {
+                        avail = s->device_available();
+                        asked = true;
+                    }
+                    if (sb > avail) {  // the device cannot hold its staging now
+                        if (s->expire_short_head(others)) continue;
+                        break;
+                    }
+                    avail -= sb;
+                }
                 s->pending.pop_front();
                 s->inflight += t.bytes;
                 s->peak = std::max(s->peak, s->inflight);
@@ -298,6 +374,17 @@ void server_loop(Server *s) {
                 lk.unlock();
                 int rc = run_plain(s, id);
                 lk.lock();
+                if (rc == MQ_ERR_OOM) {  // nothing was launched: back to the head of the queue
+                    s->inflight -= t.bytes;
+                    s->pending.push_front(id);
+                    s->plain_outstanding.fetch_sub(1);
+                    --s->batches;
+                    --s->batch_jobs;
+                    ++s->deferred;
+                    s->expire_short_head(s->plain_outstanding.load() > 0);
+                    break;
+                }
+                s->short_since = 0;
                 if (rc) {
                     s->finish(id, rc, now_ns());
                     s->plain_outstanding.fetch_sub(1);
@@ -312,15 +399,32 @@ void server_loop(Server *s) {
                     if ((double)age < s->cfg.linger_us * 1e3 && any_busy) break;
                 }
                 std::vector<mq_job> jobs;
+                size_t staging = 0, avail = 0;
+                bool asked = false, short_of_memory = false;
                 while (!s->pending.empty() && jobs.size() < s->cfg.max_batch_jobs) {
                     Ticket &t = s->ticket(s->pending.front());
-                    if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes) break;  // wait for memory to free up
+                    if (s->inflight + t.bytes > s->cfg.hbm_budget_bytes) break;  // wait for the budget to free up
+                    const size_t sb = job_scratch_bytes(t.job);
+                    if (sb) {  // staging comes from device memory: take it only while the device has it
+                        if (!asked) {
+                            avail = s->device_available();
+                            asked = true;
+                        }
+                        if (staging + sb > avail) {
+                            short_of_memory = true;
+                            break;
+                        }
+                        staging += sb;
+                    }
                     s->inflight += t.bytes;
                     jobs.push_back(t.job);
                     sl->tickets.push_back(s->pending.front());
                     s->pending.pop_front();
                 }
-                if (jobs.empty()) break;
+                if (jobs.empty()) {
+                    if (short_of_memory && s->expire_short_head(any_busy)) continue;
+                    break;
+                }
                 s->peak = std::max(s->peak, s->inflight);
                 sl->busy.store(true);
                 ++s->batches;
@@ -328,6 +432,22 @@ void server_loop(Server *s) {
                 lk.unlock();
                 int rc = launch_batch(s, sl, jobs);
                 lk.lock();
+                if (rc == MQ_ERR_OOM) {  // nothing was launched: the requests go back to the head of the queue
+                    for (auto it = sl->tickets.rbegin(); it != sl->tickets.rend(); ++it) {
+                        s->inflight -= s->ticket(*it).bytes;
+                        s->pending.push_front(*it);
+                    }
+                    s->deferred += sl->tickets.size();
+                    --s->batches;
+                    s->batch_jobs -= jobs.size();
+                    sl->tickets.clear();
+                    sl->busy.store(false);
+                    bool in_flight = false;
+                    for (Slot *o : s->slots) in_flight |= o->busy.load();
+                    s->expire_short_head(in_flight);
+                    break;
+                }
+                if (!rc) s->short_since = 0;  // a batch launched: the shortage, if any, is over
                 if (rc) {
                     const uint64_t t = now_ns();
                     for (uint64_t id : sl->tickets) s->finish(id, rc, t);
@@ -357,12 +477,20 @@ extern "C" int mq_server_create(mq_server **out, const mq_server_cfg *cfg) {
         delete s;
         return mq_fail(MQ_ERR_ARG, "unknown server mode %d", s->cfg.mode);
     }
-    cudaGetDevice(&s->device);
+    cudaError_t ge = cudaGetDevice(&s->device);
+    if (ge != cudaSuccess) {
+        delete s;
+        return mq_cuda_fail(ge, "cudaGetDevice");
+    }
     if (s->cfg.hbm_budget_bytes == 0) {
         size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
+        if ((ge = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) {
+            delete s;
+            return mq_cuda_fail(ge, "cudaMemGetInfo");
+        }
         s->cfg.hbm_budget_bytes = fr / 2;
     }
+    if (s->cfg.reserve_bytes == 0) s->cfg.reserve_bytes = (size_t)256 << 20;
     if (s->cfg.slots == 0) s->cfg.slots = 2;
     if (s->cfg.max_batch_jobs == 0) s->cfg.max_batch_jobs = 4096;
     if (s->cfg.wait_timeout_s <= 0) s->cfg.wait_timeout_s = 2.0;
@@ -459,6 +587,36 @@ extern "C" int mq_server_poisson(mq_server *srv, const mq_job *pool, size_t npoo
     return MQ_OK;
 }
 
+extern "C" int mq_cancel(mq_server *srv, uint64_t ticket) {
+    if (!srv) return mq_fail(MQ_ERR_ARG, "NULL server");
+    Server *s = srv->impl;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (ticket == 0 || ticket > s->tickets.size())
+            return mq_fail(MQ_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+        auto it = std::find(s->pending.begin(), s->pending.end(), ticket);
+        if (it == s->pending.end())
+            return mq_fail(MQ_ERR_STATE, "ticket %llu is no longer queued (launched or finished)",
+                           (unsigned long long)ticket);
+        s->pending.erase(it);
+        Ticket &t = s->ticket(ticket);
+        t.done = true;
+        t.status = MQ_ERR_CANCELLED;
+        t.t_done = now_ns();
+        ++s->cancelled;
+    }
+    s->done_cv.notify_all();
+    s->cv.notify_all();
+    return MQ_OK;
+}
+
+extern "C" int mq_server_inject_alloc_failures(mq_server *srv, unsigned n) {
+    if (!srv) return mq_fail(MQ_ERR_ARG, "NULL server");
+    srv->impl->inject_fail.store(n);
+    srv->impl->cv.notify_all();
+    return MQ_OK;
+}
+
 extern "C" int mq_poll(mq_server *srv, uint64_t ticket, int *done, int *status) {
     if (!srv || !done) return mq_fail(MQ_ERR_ARG, "NULL argument");
     Server *s = srv->impl;
@@ -510,6 +668,8 @@ extern "C" int mq_server_stats(mq_server *srv, mq_stats *out) {
     out->completed = s->completed;
     out->failed = s->failed;
     out->batches = s->batches;
+    out->cancelled = s->cancelled;
+    out->deferred = s->deferred;
     out->peak_inflight_bytes = s->peak;
     out->mean_batch_jobs = s->batches ? (double)s->batch_jobs / (double)s->batches : 0.0;
     std::vector<double> v = s->lat_ms;
@@ -540,7 +700,7 @@ extern "C" int mq_server_reset_stats(mq_server *srv) {
     Server *s = srv->impl;
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_ms.clear();
-    s->completed = s->failed = s->batches = s->batch_jobs = 0;
+    s->completed = s->failed = s->batches = s->batch_jobs = s->cancelled = s->deferred = 0;
     s->t_first = s->t_last = 0;
     s->bfly = s->mm = 0;
     s->peak = s->inflight;

@@ -21,6 +21,7 @@ from . import _build
 MQ_OK = 0
 MQ_ERR_ARG, MQ_ERR_MODULUS, MQ_ERR_ROOT, MQ_ERR_SIZE, MQ_ERR_ALIGN = -1, -2, -3, -4, -5
 MQ_ERR_OOM, MQ_ERR_CUDA, MQ_ERR_TIMEOUT, MQ_ERR_RANGE, MQ_ERR_STATE = -6, -7, -8, -9, -10
+MQ_ERR_CANCELLED = -11
 MQ_W64, MQ_W128, MQ_W192, MQ_W256 = 1, 2, 3, 4
 MQ_NEGACYCLIC, MQ_CYCLIC, MQ_ORDER_NATURAL, MQ_ORDER_BITREV = 0, 1, 0, 2
 MQ_CHECK_INPUTS = 0x100   # plan flag, or OR-ed into a BLAS width: range-check the inputs first
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = False):
         "mq_server_drain": [_vp, ctypes.c_double],
         "mq_server_poisson": [_vp, _vp, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                               ctypes.POINTER(ctypes.c_double)],
+        "mq_cancel": [_vp, ctypes.c_uint64],
+        "mq_server_inject_alloc_failures": [_vp, ctypes.c_uint],
         "mq_server_stats": [_vp, _vp],
         "mq_server_reset_stats": [_vp],
         "mq_server_destroy": [_vp],
@@ -339,7 +342,8 @@ MQ_SERVE_BATCHED, MQ_SERVE_PLAIN = 0, 1
 
 class mq_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("slots", ctypes.c_uint), ("max_batch_jobs", ctypes.c_uint),
-                ("linger_us", ctypes.c_double), ("wait_timeout_s", ctypes.c_double), ("mode", ctypes.c_int)]
+                ("linger_us", ctypes.c_double), ("wait_timeout_s", ctypes.c_double), ("mode", ctypes.c_int),
+                ("reserve_bytes", ctypes.c_size_t)]
 
 
 class mq_stats(ctypes.Structure):
@@ -348,7 +352,8 @@ class mq_stats(ctypes.Structure):
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("span_s", ctypes.c_double),
                 ("jobs_per_s", ctypes.c_double), ("butterflies_per_s", ctypes.c_double),
                 ("modmul_per_s", ctypes.c_double), ("mean_batch_jobs", ctypes.c_double),
-                ("peak_inflight_bytes", ctypes.c_size_t)]
+                ("peak_inflight_bytes", ctypes.c_size_t), ("cancelled", ctypes.c_uint64),
+                ("deferred", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -376,6 +381,14 @@ def mq_submit(server: Server, job: mq_job) -> int:
     t = ctypes.c_uint64()
     _check(load().mq_submit(server.handle, ctypes.cast(ctypes.byref(job), _vp), ctypes.byref(t)))
     return t.value
+
+
+def mq_cancel(server: Server, ticket: int):
+    _check(load().mq_cancel(server.handle, ticket))
+
+
+def mq_server_inject_alloc_failures(server: Server, n: int):
+    _check(load().mq_server_inject_alloc_failures(server.handle, n))
 
 
 def mq_poll(server: Server, ticket: int):

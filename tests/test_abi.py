@@ -142,3 +142,42 @@ def test_checked_blas_still_rejects_bad_arguments_first(lib):
     with pytest.raises(M.MqError) as e:   # misaligned pointer
         M.mod_vadd(8, 16, 16, 4, 2**61 + 1, M.MQ_W128 | M.MQ_CHECK_INPUTS, stream=0)
     assert e.value.code == M.MQ_ERR_ALIGN
+
+
+def _header_structs():
+    """typedef struct NAME { ... } NAME; of every header: NAME -> field names in order."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"typedef\s+struct\s+(\w+)\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+            fields = []
+            for decl in m.group(2).split(";"):
+                decl = decl.strip()
+                if not decl:
+                    continue
+                first, *rest = decl.split(",")      # "type a, b[2], *c" -> a, b, c
+                names = [first.split()[-1]] + [r.strip() for r in rest]
+                fields += [re.sub(r"\[.*\]", "", n).lstrip("*") for n in names]
+            out[m.group(1)] = fields
+    return out
+
+
+def test_binding_structs_follow_the_header():
+    """Every structure the binding passes through the ABI lists the header's fields, in order."""
+    checked = 0
+    for name, fields in _header_structs().items():
+        cls = getattr(M, name, None)
+        if cls is None:
+            continue
+        assert [f for f, _ in cls._fields_] == fields, name
+        checked += 1
+    assert checked >= 4   # mq_job, mq_batch_opts, mq_server_cfg, mq_stats
+
+
+def test_binding_error_codes_follow_the_header():
+    text = open(os.path.join(ROOT, "include", "mqntt.h")).read()
+    codes = dict(re.findall(r"#define (MQ_ERR_\w+) \((-\d+)\)", text))
+    assert len(codes) >= 11
+    for name, v in codes.items():
+        assert getattr(M, name) == int(v), name
+    assert len(set(codes.values())) == len(codes)
