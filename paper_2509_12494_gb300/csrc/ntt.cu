@@ -1,11 +1,64 @@
 // ntt.cu -- twiddle-table construction and the dispatch of transform passes to the kernels
 // instantiated in ntt_w{64,128}_{fwd,inv}.cu (the kernels themselves are in ntt_kernel.cuh).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "wide.cuh"
 
 namespace mq {
+
+namespace ntt_detail {
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of one side of a TMA pass over 128-bit residues with tiles of 2^8 (tma.cuh):
+//   column view: dims (2 N2 words of a row, N1 rows, batch), strides (16 N2, 16 stride) bytes,
+//     box 16 words x 256 rows -- element l of 8 adjacent columns per 128-byte row;
+//   row view: dims (16 words, N / 8 rows of 128 bytes, batch), strides (128, 16 stride), box
+//     16 words x 256 rows -- 8 consecutive rows of 2^8 residues.
+// Both with the 128-byte swizzle.  Returns 0, or nonzero when the map cannot be made.
+int tile_map(CUtensorMap *m, bool col, const void *base, int logN, int L1, unsigned long long batch, size_t stride) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return -1;
+    const int L2 = logN - L1;
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3] = {16, 256, 1}, es[3] = {1, 1, 1};
+    if (col) {
+        dims[0] = 2ull << L2;
+        dims[1] = 1ull << L1;
+        strides[0] = (1ull << L2) * 16;
+    } else {
+        dims[0] = 16;
+        dims[1] = (1ull << logN) / 8;
+        strides[0] = 128;
+    }
+    dims[2] = batch;
+    strides[1] = (cuuint64_t)stride * 16;
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+}  // namespace ntt_detail
 
 cudaError_t launch_ntt_w3_fwd(int L, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_ntt_w3_inv(int L, const PassArgs &a, cudaStream_t s);

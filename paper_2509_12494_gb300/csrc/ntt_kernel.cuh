@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 #include "wide.cuh"
 
 namespace mq {
@@ -260,14 +261,24 @@ __device__ __forceinline__ void stage_twiddles_async(const PassArgs &a, unsigned
     }
 }
 
+// Shared-memory index of element l of a tile: the tile's own swizzled array, or (XCOL) element l
+// of tile gx in a column-view TMA group of 8 tiles, [l][gx ^ (l & 7)] (tma.cuh).
+template <int W, bool XCOL>
+__device__ __forceinline__ int tile_index(int l, int gx) {
+    return XCOL ? ((l << 3) | (gx ^ (l & 7))) : swz<W>(l);
+}
+
 // One register round: stages s_begin .. s_begin + RR - 1 of a tile of 2^L residues, each thread
 // holding R residues (R / 2^RR independent groups of 2^RR), read from and written back to the
 // shared-memory tile, then a barrier (of the warp when one warp holds the tile).  s_begin is a runtime value so that all full rounds share
 // this code (the instruction footprint matters when several kernels' tiles share one SM).
-template <int W, int L, int RR, bool INV, int BAR = 0, int RL = 0>
+// XCOL: the tile is tile gx of a column-view TMA group, whose threads span the CTA's warps (the
+// round ends with a CTA barrier); CANON: the last round of a final pass, which leaves canonical
+// residues (below q) in shared memory for the copy engine to store.
+template <int W, int L, int RR, bool INV, int BAR = 0, int RL = 0, bool XCOL = false, bool CANON = false>
 __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W>::E *tile, int t, unsigned tw_base,
                                             int s_begin, const typename Traits<W>::TW *tw, typename Traits<W>::E q,
-                                            typename Traits<W>::E q8, typename Traits<W>::E nq) {
+                                            typename Traits<W>::E q8, typename Traits<W>::E nq, int gx = 0) {
     typedef Traits<W> Tr;
     typedef typename Tr::E E;
     typedef Shape<W, L, RL> S;
@@ -281,7 +292,7 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
         int lo = vt & ((1 << b_lo) - 1), hi = vt >> b_lo;
         base[k] = (hi << (b_hi + 1)) | lo;
 #pragma unroll
-        for (int e = 0; e < (1 << RR); ++e) x[k * (1 << RR) + e] = tile[swz<W>(base[k] | (e << b_lo))];
+        for (int e = 0; e < (1 << RR); ++e) x[k * (1 << RR) + e] = tile[tile_index<W, XCOL>(base[k] | (e << b_lo), gx)];
     }
 #pragma unroll
     for (int jj = 0; jj < RR; ++jj) {
@@ -324,15 +335,26 @@ __device__ __forceinline__ void radix_round(const PassArgs &a, typename Traits<W
             }
         }
     }
+    if constexpr (CANON) {  // forward values are below 16q, inverse ones below 8q
+        const E q2 = add_nored(q, q), q4 = add_nored(q2, q2);
+#pragma unroll
+        for (int i = 0; i < S::R; ++i) {
+            E v = x[i];
+            if (!INV) v = csub(v, q8);
+            v = csub(v, q4);
+            v = csub(v, q2);
+            x[i] = csub(v, q);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < V; ++k) {
 #pragma unroll
-        for (int e = 0; e < (1 << RR); ++e) tile[swz<W>(base[k] | (e << b_lo))] = x[k * (1 << RR) + e];
+        for (int e = 0; e < (1 << RR); ++e) tile[tile_index<W, XCOL>(base[k] | (e << b_lo), gx)] = x[k * (1 << RR) + e];
     }
     // A tile's TPT threads are consecutive: when they fit in one warp the next round reads only
     // what this warp wrote, and a warp barrier (which orders shared memory among its threads)
     // suffices; the warps of a CTA then drift apart between rounds instead of waiting for each other.
-    if (S::TPT <= 32)
+    if (S::TPT <= 32 && !XCOL)
         __syncwarp();
     else
         tile_sync<BAR, S::NT>();
@@ -513,6 +535,177 @@ cudaError_t launch_one(const PassArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------------
+// The TMA form of the throughput pass (128-bit residues, tiles of 2^8): each CTA group of 8 tiles
+// arrives as one tensor copy into a 1024-byte aligned buffer and leaves as one (tma.cuh), so the
+// threads only transform.  Column view: the group lands as [l][c ^ (l & 7)]; thread (g, t) =
+// (tid & 7, tid >> 3) works on tile g, so that each quarter-warp touches the 8 tiles at one
+// element, conflict-free, and rounds end with a CTA barrier (a tile's threads span the warps).
+// Row view: the group lands as 8 swizzled tiles, each held by one warp as in the cp.async form.
+// The last round of a final pass leaves canonical residues for the store.
+// ------------------------------------------------------------------------------------------------
+
+constexpr int TMA_L = 8;
+constexpr unsigned TMA_GROUP_BYTES = Shape<2, TMA_L>::G * Shape<2, TMA_L>::T * 16;  // 32 KiB
+constexpr size_t TMA_SMEM = 2 * (size_t)TMA_GROUP_BYTES + 1024;                      // + alignment
+constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;  // bound of a copy wait (never reached)
+
+// Fault word of the TMA pass (one per translation unit): the group index + 1 of a copy wait that
+// gave up, after which the kernel stops.  Not expected to be set: a tensor copy of an in-bounds
+// box always completes; the bound only keeps a broken copy from hanging the GPU.
+static __device__ unsigned long long g_tma_fault;
+
+// Tensor map of one side of a pass (host; ntt.cu).  col: the column view, else the row view.
+// Returns 0, or nonzero when the driver refuses the map (the caller takes the cp.async form).
+int tile_map(CUtensorMap *m, bool col, const void *base, int logN, int L1, unsigned long long batch, size_t stride);
+
+// Box coordinates of group `grp` (8 tiles): (x words, y rows, polynomial)
+template <bool COL>
+__device__ __forceinline__ void tma_coords(const TileAddr &ta, unsigned long long grp, int &x, int &y, int &z) {
+    constexpr int G = Shape<2, TMA_L>::G, T = Shape<2, TMA_L>::T;
+    const unsigned long long gt = grp * G;
+    const unsigned ti = (unsigned)(gt & ta.mask);
+    z = (int)(gt >> ta.lgTP);
+    x = COL ? (int)(2 * ti) : 0;
+    y = COL ? 0 : (int)(ti * (T / 8));
+}
+
+template <bool INV, bool COL>
+__device__ __forceinline__ void tma_rounds(const PassArgs &a, uint4 *buf, unsigned long long gt0, int tid) {
+    typedef Traits<2> Tr;
+    typedef Tr::E E;
+    typedef Shape<2, TMA_L> S;
+    constexpr int L = TMA_L, r = S::r, FULL = L / r, PART = L - FULL * r;
+    static_assert(PART > 0 && S::TPT == 32 && S::G == 8, "the TMA form's round schedule is that of tiles of 2^8");
+    const E q = Tr::make(a.q);
+    const E q2 = add_nored(q, q), q4 = add_nored(q2, q2);
+    const E q8 = add_nored(q4, q4);
+    const E nq = neg(q);
+    const Tw128 *tw = reinterpret_cast<const Tw128 *>(a.tw);
+    const int g = COL ? (tid & 7) : (tid >> 5), t = COL ? (tid >> 3) : (tid & 31);
+    E *tile = COL ? buf : buf + g * S::T;
+    const unsigned tw_base = COL ? 1u : tile_tw_base(a, gt0 + g);
+    if (!INV) {
+#pragma unroll 1
+        for (int rho = 0; rho < FULL; ++rho)
+            radix_round<2, L, r, false, 0, 0, COL, false>(a, tile, t, tw_base, rho * r, tw, q, q8, nq, g);
+        if (a.final) radix_round<2, L, PART, false, 0, 0, COL, true>(a, tile, t, tw_base, FULL * r, tw, q, q8, nq, g);
+        else radix_round<2, L, PART, false, 0, 0, COL, false>(a, tile, t, tw_base, FULL * r, tw, q, q8, nq, g);
+    } else {
+        radix_round<2, L, PART, true, 0, 0, COL, false>(a, tile, t, tw_base, FULL * r, tw, q, q8, nq, g);
+#pragma unroll 1
+        for (int rho = FULL - 1; rho >= 1; --rho)
+            radix_round<2, L, r, true, 0, 0, COL, false>(a, tile, t, tw_base, rho * r, tw, q, q8, nq, g);
+        if (a.final) radix_round<2, L, r, true, 0, 0, COL, true>(a, tile, t, tw_base, 0, tw, q, q8, nq, g);
+        else radix_round<2, L, r, true, 0, 0, COL, false>(a, tile, t, tw_base, 0, tw, q, q8, nq, g);
+    }
+}
+
+// A pass over `groups` groups by a persistent grid, double-buffered: thread 0 issues the next
+// group's tensor copy while the CTA transforms the current one, and the store of each group.
+template <bool INV, bool COL>
+__global__ void __launch_bounds__(256, 3)
+    ntt_pass_tma_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_out,
+                        const PassArgs a, unsigned long long groups) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    unsigned char *p = smem_raw + ((1024u - (tma::su32(smem_raw) & 1023u)) & 1023u);
+    uint4 *const buf0 = reinterpret_cast<uint4 *>(p), *const buf1 = reinterpret_cast<uint4 *>(p + TMA_GROUP_BYTES);
+    const TileAddr ta(a);
+    unsigned long long grp = blockIdx.x;
+    if (tid == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::mbar_init_fence();
+        tma::prefetch_map(&tm_in);
+        tma::prefetch_map(&tm_out);
+        if (grp < groups) {
+            int x, y, z;
+            tma_coords<COL>(ta, grp, x, y, z);
+            tma::mbar_expect(&bar[0], TMA_GROUP_BYTES);
+            tma::load3(buf0, &tm_in, x, y, z, &bar[0]);
+        }
+    }
+    __syncthreads();
+    unsigned ph0 = 0, ph1 = 0;
+    bool odd = false;
+    for (; grp < groups; grp += gridDim.x, odd = !odd) {
+        uint4 *cur = odd ? buf1 : buf0, *nxt = odd ? buf0 : buf1;
+        uint64_t *bc = odd ? &bar[1] : &bar[0], *bn = odd ? &bar[0] : &bar[1];
+        const unsigned ph = odd ? ph1 : ph0;
+        const unsigned long long next = grp + gridDim.x;
+        if (tid == 0) {
+            if (next < groups) {
+                tma::store_wait_read();  // the other buffer's store has read it
+                int x, y, z;
+                tma_coords<COL>(ta, next, x, y, z);
+                tma::mbar_expect(bn, TMA_GROUP_BYTES);
+                tma::load3(nxt, &tm_in, x, y, z, bn);
+            }
+            s_ok = tma::mbar_wait(bc, ph, TMA_WAIT_NS);
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (tid == 0) atomicCAS(&g_tma_fault, 0ull, grp + 1);
+            break;
+        }
+        while (!tma::mbar_test(bc, ph)) {  // completed: thread 0 saw it
+        }
+        if (odd) ph1 ^= 1;
+        else ph0 ^= 1;
+        tma_rounds<INV, COL>(a, cur, grp * Shape<2, TMA_L>::G, tid);
+        tma::fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            int x, y, z;
+            tma_coords<COL>(ta, grp, x, y, z);
+            tma::store3(&tm_out, x, y, z, cur);
+            tma::store_commit();
+        }
+    }
+    if (tid == 0) tma::store_wait();
+}
+
+// Whether a pass of tiles of 2^8 over 128-bit residues can take the TMA form: both sides in the
+// column view or both in the unpermuted row view, with at least one group of 8 tiles per
+// polynomial (groups never straddle polynomials) and coordinates that fit 32 bits.
+inline bool tma_eligible(const PassArgs &a) {
+    if (a.batch == 0 || a.batch >= (1ull << 31)) return false;
+    if (a.col) return a.in_layout == LAYOUT_COL && a.out_layout == LAYOUT_COL && a.L1 == TMA_L && a.logN - a.L1 >= 3;
+    return a.in_layout == LAYOUT_ROW && a.out_layout == LAYOUT_ROW && !a.perm && a.logN - a.L1 == TMA_L && a.L1 >= 3;
+}
+
+template <bool INV>
+cudaError_t launch_tma(const PassArgs &a, cudaStream_t s, bool *taken) {
+    *taken = false;
+    if (!tma_eligible(a)) return cudaSuccess;
+    const unsigned long long groups = pass_tiles(a) / Shape<2, TMA_L>::G;
+    if (groups < (unsigned long long)sm_count()) return cudaSuccess;  // small passes: the latency shape
+    CUtensorMap mi, mo;
+    if (tile_map(&mi, a.col != 0, a.in, a.logN, a.L1, a.batch, a.in_stride) ||
+        tile_map(&mo, a.col != 0, a.out, a.logN, a.L1, a.batch, a.out_stride))
+        return cudaSuccess;
+    static int per_sm[2] = {0, 0};  // benign race: every thread computes the same values
+    const int c = a.col ? 1 : 0;
+    if (per_sm[c] == 0) {
+        auto k = a.col ? ntt_pass_tma_kernel<INV, true> : ntt_pass_tma_kernel<INV, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, TMA_SMEM);
+        if (e != cudaSuccess) return e;
+        per_sm[c] = n > 0 ? n : 1;
+    }
+    const unsigned long long wave = (unsigned long long)sm_count() * per_sm[c];
+    const unsigned grid = (unsigned)(groups < wave ? groups : wave);
+    if (a.col) ntt_pass_tma_kernel<INV, true><<<grid, 256, TMA_SMEM, s>>>(mi, mo, a, groups);
+    else ntt_pass_tma_kernel<INV, false><<<grid, 256, TMA_SMEM, s>>>(mi, mo, a, groups);
+    *taken = true;
+    return cudaGetLastError();
+}
+
 // Residues per thread of the latency shape: radix-4 rounds.  Measured on a single transform of
 // 2^10 (124-bit, forward + inverse): 13.6 us with radix-2 rounds, 12.1 with radix-4, 16.1 with
 // radix-8 (fewer warps per tile).
@@ -524,6 +717,11 @@ constexpr int LATENCY_RADIX = 4;
 // and tiles of 2^5 to 2^10 (larger tiles already take a CTA each in the throughput shape).
 template <int W, int L, bool INV>
 cudaError_t launch_pass(const PassArgs &a, cudaStream_t s) {
+    if constexpr (W == 2 && L == TMA_L) {
+        bool taken = false;
+        cudaError_t e = launch_tma<INV>(a, s, &taken);
+        if (e != cudaSuccess || taken) return e;
+    }
     if constexpr (W <= 2 && L >= 5 && L <= 10) {
         const unsigned long long groups = (pass_tiles(a) + Shape<W, L>::G - 1) / Shape<W, L>::G;
         if (groups < (unsigned long long)sm_count()) return launch_one<W, L, INV, LATENCY_RADIX>(a, s);
