@@ -216,6 +216,13 @@ static int fill_job(const mq_job &j, size_t index, const mq_batch_opts &o, void 
                 d.L[0] = L2;
                 d.L[1] = L1;
             }
+            // passes of 128-bit tiles of 2^8 in the column or unpermuted row view take the TMA form
+            for (int k = 0; k < 2; ++k) {
+                const PassArgs &a = d.pa[k];
+                d.tma[k] = d.width == MQ_W128 && d.L[k] == TMA_L && tma_eligible(a) &&
+                           tile_map(&d.tm[k][0], a.col != 0, a.in, a.logN, a.L1, a.batch, a.in_stride) == 0 &&
+                           tile_map(&d.tm[k][1], a.col != 0, a.out, a.logN, a.L1, a.batch, a.out_stride) == 0;
+            }
         }
         return MQ_OK;
     }
@@ -284,6 +291,8 @@ int mq::batch_detail::refill_jobs(const mq_job *jobs, size_t njobs, const mq_bat
         d.n_items = io[i].n_items;  // counters and item bookkeeping stay those of the build
         d.poly_base = io[i].poly_base;
         d.groups0 = io[i].groups0;
+        if (d.tma[0] != io[i].tma[0] || d.tma[1] != io[i].tma[1])  // the items' copy form is fixed at build
+            return mq_fail(MQ_ERR_ARG, "job %zu: the update changes how its passes are staged", i);
         io[i] = d;
     }
     return MQ_OK;
@@ -341,7 +350,8 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
             k.key = chain_pos[k.chain] + (unsigned long long)k.stage * lag_items;
             k.it.job = (unsigned)i;
             k.it.pass = (unsigned short)pass;
-            k.it.meta = (unsigned short)item_meta(d.kind == JK_BLAS, d.width, d.inv != 0, d.kind == JK_NTT ? d.L[pass] : 0);
+            k.it.meta = (unsigned short)item_meta(d.kind == JK_BLAS, d.width, d.inv != 0, d.kind == JK_NTT ? d.L[pass] : 0,
+                                                  d.kind == JK_NTT && d.tma[pass] != 0);
             k.it.poly = poly;
             k.it.dep = k.it.target = k.it.bump = 0;  // resolved once every job's item count is known
             k.it.first = first;

@@ -33,6 +33,8 @@ struct JobDev {
     unsigned long long chunk;  // BLAS: residues per item
     PassArgs pa[2];            // NTT passes
     BlasArgs ba;               // BLAS operands
+    int tma[2];                // pass p takes the TMA form (tma.cuh); its tensor maps follow
+    alignas(64) CUtensorMap tm[2][2];  // [pass][0: source, 1: destination]
 };
 
 // One work item (32 bytes; the prefetching kernel copies it into shared memory with two 16-byte
@@ -43,7 +45,7 @@ struct ItemDev {
     unsigned job;
     unsigned short pass;
     unsigned short meta;  // what the kernel needs to pick its code path without reading the job
-                          // descriptor: ITEM_BLAS | ITEM_W128 | ITEM_INV | (tile log size << 4)
+                          // descriptor: ITEM_BLAS | ITEM_W128 | ITEM_INV | ITEM_TMA | (tile log size << 4)
     unsigned poly;
     unsigned dep;     // counter this item waits for, 0: none
     unsigned target;  // value the dependency counter must reach
@@ -51,9 +53,10 @@ struct ItemDev {
     unsigned long long first;  // NTT: first tile of the pass; BLAS: chunk index
 };
 static_assert(sizeof(ItemDev) == 32, "work items are copied as two 16-byte halves");
-constexpr unsigned ITEM_BLAS = 1, ITEM_W128 = 2, ITEM_INV = 4;
-__host__ __device__ constexpr unsigned item_meta(bool blas, int width, bool inv, int L) {
-    return (blas ? ITEM_BLAS : 0u) | (width == 2 ? ITEM_W128 : 0u) | (inv ? ITEM_INV : 0u) | ((unsigned)L << 4);
+constexpr unsigned ITEM_BLAS = 1, ITEM_W128 = 2, ITEM_INV = 4, ITEM_TMA = 8;
+__host__ __device__ constexpr unsigned item_meta(bool blas, int width, bool inv, int L, bool tma = false) {
+    return (blas ? ITEM_BLAS : 0u) | (width == 2 ? ITEM_W128 : 0u) | (inv ? ITEM_INV : 0u) | (tma ? ITEM_TMA : 0u) |
+           ((unsigned)L << 4);
 }
 
 // Host-side expansion of a job list into the device tables of one launch.

@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PassArgs s_pa[2];
     __shared__ BlasArgs s_ba[2];
+    __shared__ __align__(8) uint64_t s_bar[2];  // tensor copies into buffer 0 / 1 (TMA items)
     __shared__ __align__(16) ItemDev s_rec[3];  // records of items k, k + 1, k + 2 (slot k % 3)
     __shared__ unsigned s_idx[3];               // their indices (n_items: none)
     // whether item k + 1's dependency was met when item k started, by the parity of k: thread 0 writes
@@ -331,8 +332,19 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     const int tid = threadIdx.x;
     unsigned *status = ctrs + 1;
     (void)njobs;
+    // Instantiations with 128-bit transforms carry TMA items (ITEM_TMA): their buffers start on a
+    // 1024-byte boundary (the 128-byte swizzle's period), buf_bytes apart, a multiple of 1024.
+    constexpr bool TMA = (WM & 2) != 0;
+    unsigned char *const smem = TMA ? smem_raw + ((1024u - (tma::su32(smem_raw) & 1023u)) & 1023u) : smem_raw;
+    unsigned ph0 = 0, ph1 = 0;  // all threads: phase parity of the next tensor copy into buffer 0 / 1
+    if (TMA && tid == 0) {
+        tma::mbar_init(&s_bar[0], 1);
+        tma::mbar_init(&s_bar[1], 1);
+        tma::mbar_init_fence();
+    }
 
-    // all threads: copy the item's arguments and start staging its tiles into buffer b
+    // all threads: copy the item's arguments and start staging its tiles into buffer b (a TMA item:
+    // thread 0 issues its tensor copy, after the dependency it acquired)
     auto stage = [&](int b, const ItemDev &item) {
         const JobDev *J = jobs + item.job;
         const unsigned m = item.meta;  // kind, width and tile size without a read of the job descriptor
@@ -341,8 +353,16 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
             const unsigned *src = reinterpret_cast<const unsigned *>(&pa);
             unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
             for (int w = tid; w < (int)(sizeof(PassArgs) / 4); w += BT) dst[w] = src[w];
-            unsigned char *buf = smem_raw + b * buf_bytes;
-            if ((WM & 1) && (!(WM & 2) || !(m & ITEM_W128)))
+            unsigned char *buf = smem + b * buf_bytes;
+            if (TMA && (m & ITEM_TMA)) {
+                if (tid == 0) {
+                    int x, y, z;
+                    ntt_detail::tma_box(ntt_detail::TileAddr(pa), pa.col != 0, item.first, x, y, z);
+                    tma::fence_async_global();
+                    tma::mbar_expect(&s_bar[b], ntt_detail::TMA_GROUP_BYTES);
+                    tma::load3(buf, &J->tm[item.pass][0], x, y, z, &s_bar[b]);
+                }
+            } else if ((WM & 1) && (!(WM & 2) || !(m & ITEM_W128)))
                 stage_tiles<1, BT, true>((int)(m >> 4), pa, item.first, buf, tid);
             else if (WM & 2)
                 stage_tiles<2, BT>((int)(m >> 4), pa, item.first, buf, tid);
@@ -363,7 +383,13 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
 
     unsigned pend = 0;  // thread 0: index of the item after the two whose records are in flight
     unsigned pend_bump = 0, pend_job = 0;  // thread 0: completion counters not yet incremented (0: none)
+    bool pend_tma = false;                 // thread 0: that item's results leave by a tensor store
     auto signal_pending = [&]() {
+        if (pend_tma) {  // the store has landed, and is ordered before the release below
+            tma::store_wait();
+            tma::fence_async_global();
+            pend_tma = false;
+        }
         if (pend_bump) red_release_add(ctrs + pend_bump);
         if (pend_job) red_release_add(ctrs + pend_job);
         pend_bump = pend_job = 0;
@@ -388,6 +414,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
         if (s_idx[r] >= n_items) break;
         if (tid == 0) {
             asm volatile("cp.async.wait_all;" ::: "memory");  // the record of item k + 1
+            if (TMA) tma::store_wait_read();  // item k - 1's tensor store has read buffer b ^ 1
             int ready = 1;
             if (s_idx[r1] < n_items && s_rec[r1].dep) ready = ld_acquire(ctrs + s_rec[r1].dep) >= s_rec[r1].target;
             s_ready[b] = ready;
@@ -400,7 +427,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();  // every thread's copies of the current item (and its arguments) landed
         if (tid == 0) {   // the previous item's completion, the record of item k + 2, the index of item k + 3
-            signal_pending();
+            if (!pend_tma) signal_pending();  // (one that left by a tensor store: at the end of this item)
             const unsigned i2 = pend < n_items ? pend : n_items;
             s_idx[r2] = i2;
             if (i2 < n_items) copy_record(&s_rec[r2], items + i2);
@@ -410,8 +437,32 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
 
         const ItemDev &item = s_rec[r];
         const unsigned m = item.meta;
-        unsigned char *buf = smem_raw + b * buf_bytes;
-        if (!BL || !(m & ITEM_BLAS)) {
+        unsigned char *buf = smem + b * buf_bytes;
+        const bool tma_item = TMA && (m & ITEM_TMA);
+        if (tma_item) {
+            // every thread waits (bounded) for the tensor copy; on a timeout it marks the batch
+            // failed and goes on, so that no barrier is left unmatched
+            if (!tma::mbar_wait(&s_bar[b], b ? ph1 : ph0, limit_ns)) atomicCAS(status, 0u, (unsigned)MQ_ERR_TIMEOUT);
+            if (b) ph1 ^= 1u;
+            else ph0 ^= 1u;
+            const PassArgs &pa = s_pa[b];
+            uint4 *tb = reinterpret_cast<uint4 *>(buf);
+            if (m & ITEM_INV) {
+                if (pa.col) ntt_detail::tma_rounds<true, true>(pa, tb, item.first, tid);
+                else ntt_detail::tma_rounds<true, false>(pa, tb, item.first, tid);
+            } else {
+                if (pa.col) ntt_detail::tma_rounds<false, true>(pa, tb, item.first, tid);
+                else ntt_detail::tma_rounds<false, false>(pa, tb, item.first, tid);
+            }
+            tma::fence_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                int x, y, z;
+                ntt_detail::tma_box(ntt_detail::TileAddr(pa), pa.col != 0, item.first, x, y, z);
+                tma::store3(&jobs[item.job].tm[item.pass][1], x, y, z, tb);
+                tma::store_commit();
+            }
+        } else if (!BL || !(m & ITEM_BLAS)) {
             const int L = (int)(m >> 4);
             if ((WM & 1) && (!(WM & 2) || !(m & ITEM_W128))) {
                 if (m & ITEM_INV) compute_store<1, true>(L, s_pa[b], item.first, buf, tid);
@@ -433,11 +484,25 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
         // make them visible (cumulatively) to whoever acquires the counters.  When the next item is
         // already staged, the additions wait until that item's copies have landed (below, after the
         // second barrier of the next iteration), so that their latency overlaps the next transform
-        // instead of holding every warp at the next barrier; before any wait of this CTA they are
-        // made at once, so no wait can depend on an addition this CTA has not made yet.
+        // instead of holding every warp at the next barrier -- or, for an item whose results leave
+        // by a tensor store, until the end of the next item, once that store has landed; before any
+        // wait of this CTA they are made at once (after the store), so no wait can depend on an
+        // addition this CTA has not made yet.
+        if (TMA && !tma_item) tma::fence_async_shared();  // before a later tensor copy into this buffer
         if (tid == 0) {
+            // The previous item's results, if they left by a tensor store, are released here, an
+            // item after that store was issued, so that it has landed and the wait costs nothing;
+            // this item's store (if any) stays in flight.
+            if (pend_tma) {
+                if (tma_item) tma::store_wait_all_but_last();
+                else tma::store_wait();
+                tma::fence_async_global();
+                pend_tma = false;
+                signal_pending();
+            }
             pend_bump = item.bump;
             pend_job = 2 + item.job;
+            pend_tma = tma_item;
         }
         // re-read from shared memory rather than keep registers live across the transform
         // (s_ready[b] changes only at item k + 2's start, s_idx[r1] only in the late path below)
@@ -453,7 +518,10 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
     }
-    if (tid == 0) signal_pending();  // the last item's completion
+    if (tid == 0) {
+        signal_pending();  // the last item's completion
+        if (TMA) tma::store_wait();
+    }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
@@ -495,20 +563,36 @@ struct PersistentKernel {
                               unsigned njobs, unsigned long long limit_ns, unsigned grid, size_t smem, cudaStream_t s);
 };
 
+// Bytes of one buffer and of the dynamic shared memory: the prefetching form with 128-bit
+// transforms rounds its buffers up to 1024-byte multiples and adds 1024 bytes to align the first
+// (TMA items, tma.cuh).
+template <int FORM, int W>
+constexpr size_t buffer_bytes(size_t tiles) {
+    return (FORM && W == 2) ? ((tiles > ntt_detail::TMA_GROUP_BYTES ? tiles : ntt_detail::TMA_GROUP_BYTES) + 1023) / 1024 * 1024
+                            : tiles;
+}
+template <int FORM, int W>
+constexpr size_t dynamic_bytes(size_t buf) {
+    return (FORM && W == 2) ? 2 * buf + 1024 : 2 * buf;
+}
+
 #define MQ_DEFINE_PERSISTENT_FORM(FORM, KERNEL, WM, BL)                                                   \
     template <>                                                                                            \
     cudaError_t PersistentKernel<FORM, WM, BL>::configure(int *per_sm, size_t *smem) {                     \
-        *smem = kernel_smem<KCfg<WM, BL>::W>();                                                            \
+        constexpr int W_ = KCfg<WM, BL>::W;                                                                \
+        *smem = buffer_bytes<FORM, W_>(kernel_smem<W_>());                                                 \
+        const size_t dyn = dynamic_bytes<FORM, W_>(*smem);                                                 \
         cudaError_t e = cudaFuncSetAttribute(KERNEL<WM, BL>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                             (int)(2 * *smem));                                            \
+                                             (int)dyn);                                                    \
         if (e != cudaSuccess) return e;                                                                    \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, KERNEL<WM, BL>, THREADS, 2 * *smem);  \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, KERNEL<WM, BL>, THREADS, dyn);        \
     }                                                                                                      \
     template <>                                                                                            \
     cudaError_t PersistentKernel<FORM, WM, BL>::launch(const JobDev *djobs, const ItemDev *ditems, unsigned n_items, \
                                                        unsigned *dctrs, unsigned njobs, unsigned long long limit_ns, \
                                                        unsigned grid, size_t smem, cudaStream_t s) {           \
-        KERNEL<WM, BL><<<grid, THREADS, 2 * smem, s>>>(djobs, ditems, n_items, dctrs, njobs, limit_ns, smem); \
+        const size_t dyn = dynamic_bytes<FORM, KCfg<WM, BL>::W>(smem);                                     \
+        KERNEL<WM, BL><<<grid, THREADS, dyn, s>>>(djobs, ditems, n_items, dctrs, njobs, limit_ns, smem);   \
         return cudaGetLastError();                                                                         \
     }
 

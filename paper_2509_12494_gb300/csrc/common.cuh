@@ -1,5 +1,6 @@
 // common.cuh -- types shared by the library's translation units (not part of the public ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -43,6 +44,23 @@ struct PassArgs {
     int scale;           // inverse only: fold N^-1 into global stage 0
     int final;           // last pass of the transform: store canonical residues
 };
+
+// The TMA form of a pass (tma.cuh): 128-bit residues, tiles of 2^TMA_L, each CTA group of 8 tiles
+// moved by one tensor copy each way.
+constexpr int TMA_L = 8;
+
+// Whether a pass of tiles of 2^TMA_L over 128-bit residues can take the TMA form: both sides in the
+// column view or both in the unpermuted row view, at least one group of 8 tiles per polynomial
+// (groups never straddle polynomials), and coordinates that fit 32 bits.
+inline bool tma_eligible(const PassArgs &a) {
+    if (a.batch == 0 || a.batch >= (1ull << 31)) return false;
+    if (a.col) return a.in_layout == LAYOUT_COL && a.out_layout == LAYOUT_COL && a.L1 == TMA_L && a.logN - a.L1 >= 3;
+    return a.in_layout == LAYOUT_ROW && a.out_layout == LAYOUT_ROW && !a.perm && a.logN - a.L1 == TMA_L && a.L1 >= 3;
+}
+
+// Tensor map of one side of a TMA pass (host; ntt.cu).  col: the column view, else the row view.
+// Returns 0, or nonzero when the driver refuses the map (the pass then takes the cp.async form).
+int tile_map(CUtensorMap *m, bool col, const void *base, int logN, int L1, unsigned long long batch, size_t stride);
 
 // Launch one pass; returns a cudaError_t.  L = log2 of the tile size, inv = direction.
 cudaError_t launch_ntt_pass(int width, int L, bool inv, const PassArgs &a, cudaStream_t s);

@@ -11,8 +11,6 @@
 
 namespace mq {
 
-namespace ntt_detail {
-
 // The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -57,8 +55,6 @@ int tile_map(CUtensorMap *m, bool col, const void *base, int logN, int L1, unsig
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : (int)r;
 }
-
-}  // namespace ntt_detail
 
 cudaError_t launch_ntt_w3_fwd(int L, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_ntt_w3_inv(int L, const PassArgs &a, cudaStream_t s);

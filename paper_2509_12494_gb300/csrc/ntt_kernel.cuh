@@ -545,7 +545,6 @@ cudaError_t launch_one(const PassArgs &a, cudaStream_t s) {
 // The last round of a final pass leaves canonical residues for the store.
 // ------------------------------------------------------------------------------------------------
 
-constexpr int TMA_L = 8;
 constexpr unsigned TMA_GROUP_BYTES = Shape<2, TMA_L>::G * Shape<2, TMA_L>::T * 16;  // 32 KiB
 constexpr size_t TMA_SMEM = 2 * (size_t)TMA_GROUP_BYTES + 1024;                      // + alignment
 constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;  // bound of a copy wait (never reached)
@@ -555,19 +554,13 @@ constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;  // bound of a copy wa
 // box always completes; the bound only keeps a broken copy from hanging the GPU.
 static __device__ unsigned long long g_tma_fault;
 
-// Tensor map of one side of a pass (host; ntt.cu).  col: the column view, else the row view.
-// Returns 0, or nonzero when the driver refuses the map (the caller takes the cp.async form).
-int tile_map(CUtensorMap *m, bool col, const void *base, int logN, int L1, unsigned long long batch, size_t stride);
-
-// Box coordinates of group `grp` (8 tiles): (x words, y rows, polynomial)
-template <bool COL>
-__device__ __forceinline__ void tma_coords(const TileAddr &ta, unsigned long long grp, int &x, int &y, int &z) {
-    constexpr int G = Shape<2, TMA_L>::G, T = Shape<2, TMA_L>::T;
-    const unsigned long long gt = grp * G;
+// Box coordinates (x words, y rows, polynomial) of the group of 8 tiles that starts at tile gt
+__device__ __forceinline__ void tma_box(const TileAddr &ta, bool col, unsigned long long gt, int &x, int &y, int &z) {
+    constexpr int T = Shape<2, TMA_L>::T;
     const unsigned ti = (unsigned)(gt & ta.mask);
     z = (int)(gt >> ta.lgTP);
-    x = COL ? (int)(2 * ti) : 0;
-    y = COL ? 0 : (int)(ti * (T / 8));
+    x = col ? (int)(2 * ti) : 0;
+    y = col ? 0 : (int)(ti * (T / 8));
 }
 
 template <bool INV, bool COL>
@@ -623,7 +616,7 @@ __global__ void __launch_bounds__(256, 3)
         tma::prefetch_map(&tm_out);
         if (grp < groups) {
             int x, y, z;
-            tma_coords<COL>(ta, grp, x, y, z);
+            tma_box(ta, COL, grp * Shape<2, TMA_L>::G, x, y, z);
             tma::mbar_expect(&bar[0], TMA_GROUP_BYTES);
             tma::load3(buf0, &tm_in, x, y, z, &bar[0]);
         }
@@ -640,7 +633,7 @@ __global__ void __launch_bounds__(256, 3)
             if (next < groups) {
                 tma::store_wait_read();  // the other buffer's store has read it
                 int x, y, z;
-                tma_coords<COL>(ta, next, x, y, z);
+                tma_box(ta, COL, next * Shape<2, TMA_L>::G, x, y, z);
                 tma::mbar_expect(bn, TMA_GROUP_BYTES);
                 tma::load3(nxt, &tm_in, x, y, z, bn);
             }
@@ -660,21 +653,12 @@ __global__ void __launch_bounds__(256, 3)
         __syncthreads();
         if (tid == 0) {
             int x, y, z;
-            tma_coords<COL>(ta, grp, x, y, z);
+            tma_box(ta, COL, grp * Shape<2, TMA_L>::G, x, y, z);
             tma::store3(&tm_out, x, y, z, cur);
             tma::store_commit();
         }
     }
     if (tid == 0) tma::store_wait();
-}
-
-// Whether a pass of tiles of 2^8 over 128-bit residues can take the TMA form: both sides in the
-// column view or both in the unpermuted row view, with at least one group of 8 tiles per
-// polynomial (groups never straddle polynomials) and coordinates that fit 32 bits.
-inline bool tma_eligible(const PassArgs &a) {
-    if (a.batch == 0 || a.batch >= (1ull << 31)) return false;
-    if (a.col) return a.in_layout == LAYOUT_COL && a.out_layout == LAYOUT_COL && a.L1 == TMA_L && a.logN - a.L1 >= 3;
-    return a.in_layout == LAYOUT_ROW && a.out_layout == LAYOUT_ROW && !a.perm && a.logN - a.L1 == TMA_L && a.L1 >= 3;
 }
 
 template <bool INV>

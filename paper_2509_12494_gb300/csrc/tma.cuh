@@ -86,6 +86,8 @@ __device__ __forceinline__ void store_commit() { asm volatile("cp.async.bulk.com
 __device__ __forceinline__ void store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // the thread's committed stores are complete
 __device__ __forceinline__ void store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// ... all but the most recently committed one
+__device__ __forceinline__ void store_wait_all_but_last() { asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); }
 
 // Order this thread's ordinary shared-memory accesses before later copy-engine accesses.
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
