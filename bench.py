@@ -154,8 +154,8 @@ def workload_name(wl, args):
             f"{args.bits}-bit q = 1 mod 2^{wl['log2n'] + 1}, {args.order} order")
 
 
-KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "blas_ops.cuh", "batch_internal.h", "batch_kernel.cuh",
-                  "batch.cu"]
+KERNEL_SOURCES = ["residue.cuh", "common.cuh", "ntt_kernel.cuh", "tma.cuh", "blas_ops.cuh", "batch_internal.h",
+                  "batch_kernel.cuh", "batch.cu"]
 
 
 def kernel_sources_sha256() -> str:
