@@ -416,11 +416,19 @@ int mq::batch_detail::build_tables(const mq_job *jobs, size_t njobs, const mq_ba
     }
     out.n_ctrs = 2 + njobs + poly_ctrs;
     out.variant = job_variant(jobs, njobs);
+    if (out.variant == 2) {  // 128-bit transforms only: all of them in the TMA form?
+        bool all = njobs > 0;
+        for (const JobDev &d : out.jobs) all = all && d.kind == JK_NTT && d.twopass && d.tma[0] && d.tma[1];
+        if (all) out.variant = VARIANT_TMA_ONLY;
+    }
     return MQ_OK;
 }
 
-// the instantiations: 0 the general one (any mix), 1 64-bit transforms only, 2 128-bit transforms only
-static int kernel_slot(int variant) { return variant == 1 ? 1 : variant == 2 ? 2 : 0; }
+// the instantiations: 0 the general one (any mix), 1 64-bit transforms only, 2 128-bit transforms
+// only, 3 128-bit transforms whose every pass takes the TMA form (only that code path compiled)
+static int kernel_slot(int variant) {
+    return variant == 1 ? 1 : variant == 2 ? 2 : variant == VARIANT_TMA_ONLY ? 3 : 0;
+}
 
 int mq::batch_detail::job_variant(const mq_job *jobs, size_t njobs) {
     int v = 0;
@@ -443,18 +451,22 @@ int mq::batch_detail::persistent_grid(int variant, int form, unsigned ctas_per_s
     // every instantiation gets its shared-memory limit and occupancy once per process
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
-    static int per_sm[2][3] = {};
-    static size_t buf[2][3] = {};
-    static const int max_ctas[2][3] = {
-        {PersistentKernel<0, 3, true>::MAXB, PersistentKernel<0, 1, false>::MAXB, PersistentKernel<0, 2, false>::MAXB},
-        {PersistentKernel<1, 3, true>::MAXB, PersistentKernel<1, 1, false>::MAXB, PersistentKernel<1, 2, false>::MAXB}};
+    static int per_sm[2][4] = {};
+    static size_t buf[2][4] = {};
+    static const int max_ctas[2][4] = {
+        {PersistentKernel<0, 3, true>::MAXB, PersistentKernel<0, 1, false>::MAXB, PersistentKernel<0, 2, false>::MAXB,
+         PersistentKernel<0, 6, false>::MAXB},
+        {PersistentKernel<1, 3, true>::MAXB, PersistentKernel<1, 1, false>::MAXB, PersistentKernel<1, 2, false>::MAXB,
+         PersistentKernel<1, 6, false>::MAXB}};
     std::call_once(attr_once, [&] {
-        cudaError_t e[6] = {PersistentKernel<0, 3, true>::configure(&per_sm[0][0], &buf[0][0]),
+        cudaError_t e[8] = {PersistentKernel<0, 3, true>::configure(&per_sm[0][0], &buf[0][0]),
                             PersistentKernel<0, 1, false>::configure(&per_sm[0][1], &buf[0][1]),
                             PersistentKernel<0, 2, false>::configure(&per_sm[0][2], &buf[0][2]),
+                            PersistentKernel<0, 6, false>::configure(&per_sm[0][3], &buf[0][3]),
                             PersistentKernel<1, 3, true>::configure(&per_sm[1][0], &buf[1][0]),
                             PersistentKernel<1, 1, false>::configure(&per_sm[1][1], &buf[1][1]),
-                            PersistentKernel<1, 2, false>::configure(&per_sm[1][2], &buf[1][2])};
+                            PersistentKernel<1, 2, false>::configure(&per_sm[1][2], &buf[1][2]),
+                            PersistentKernel<1, 6, false>::configure(&per_sm[1][3], &buf[1][3])};
         for (cudaError_t x : e)
             if (x != cudaSuccess && attr_err == cudaSuccess) attr_err = x;
     });
@@ -484,10 +496,12 @@ cudaError_t mq::batch_detail::launch_persistent(int variant, int form, const Job
     const int k = kernel_slot(variant);
 #define MQ_LAUNCH(F, WM, BL) return PersistentKernel<F, WM, BL>::launch(djobs, ditems, n_items, dctrs, njobs, limit_ns, grid, smem, s)
     if (form) {
+        if (k == 3) MQ_LAUNCH(1, 6, false);
         if (k == 2) MQ_LAUNCH(1, 2, false);
         if (k == 1) MQ_LAUNCH(1, 1, false);
         MQ_LAUNCH(1, 3, true);
     }
+    if (k == 3) MQ_LAUNCH(0, 6, false);
     if (k == 2) MQ_LAUNCH(0, 2, false);
     if (k == 1) MQ_LAUNCH(0, 1, false);
     MQ_LAUNCH(0, 3, true);
@@ -599,6 +613,10 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
     }
     BatchTables t;
     rc = build_tables(jobs, njobs, b->opts, b->scratch.data(), 2ull * b->grid, t);
+    if (!rc && t.variant != b->variant) {  // the TMA-only instantiation (same grid and buffers)
+        b->variant = t.variant;
+        rc = persistent_grid(b->variant, b->form, b->opts.ctas_per_sm, &b->grid, &b->smem);
+    }
     if (rc) {
         destroy_batch(b);
         return rc;

@@ -59,6 +59,10 @@ __host__ __device__ constexpr unsigned item_meta(bool blas, int width, bool inv,
            ((unsigned)L << 4);
 }
 
+// Kernel instantiation of batches of 128-bit transforms whose every pass takes the TMA form
+// (job_variant's 2 with this bit): the kernel carries only that code path.
+constexpr int VARIANT_TMA_ONLY = 2 | 8;
+
 // Host-side expansion of a job list into the device tables of one launch.
 struct BatchTables {
     std::vector<JobDev> jobs;

@@ -171,7 +171,8 @@ __device__ __forceinline__ void compute_store(int L, const PassArgs &a, unsigned
 // and stages its tiles into the buffer, and hands it over.  Warps 0-7 compute and store the item,
 // publish its completion on the counters, and free the buffer.  The producer therefore runs one
 // item ahead, and its waits and loads overlap the transform of the previous item.
-// WM: residue widths present (bit 0: 64-bit, bit 1: 128-bit); BL: BLAS jobs present.  A batch runs
+// WM: residue widths present (bit 0: 64-bit, bit 1: 128-bit; bit 2: 128-bit transforms whose every
+// item is a TMA item, prefetching form); BL: BLAS jobs present.  A batch runs
 // the narrowest instantiation that covers its jobs, which keeps registers and code small.  64-bit
 // transforms alone need fewer registers and half the shared memory, and their arithmetic has
 // shorter dependency chains per residue, so that instantiation runs one CTA per SM more (three in
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
     // Instantiations with 128-bit transforms carry TMA items (ITEM_TMA): their buffers start on a
     // 1024-byte boundary (the 128-byte swizzle's period), buf_bytes apart, a multiple of 1024.
     constexpr bool TMA = (WM & 2) != 0;
+    constexpr bool TMA_ONLY = (WM & 4) != 0;  // every item is a TMA item: only that path is compiled
     unsigned char *const smem = TMA ? smem_raw + ((1024u - (tma::su32(smem_raw) & 1023u)) & 1023u) : smem_raw;
     unsigned ph0 = 0, ph1 = 0;  // all threads: phase parity of the next tensor copy into buffer 0 / 1
     if (TMA && tid == 0) {
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
             unsigned *dst = reinterpret_cast<unsigned *>(&s_pa[b]);
             for (int w = tid; w < (int)(sizeof(PassArgs) / 4); w += BT) dst[w] = src[w];
             unsigned char *buf = smem + b * buf_bytes;
-            if (TMA && (m & ITEM_TMA)) {
+            if (TMA_ONLY || (TMA && (m & ITEM_TMA))) {
                 if (tid == 0) {
                     int x, y, z;
                     ntt_detail::tma_box(ntt_detail::TileAddr(pa), pa.col != 0, item.first, x, y, z);
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(BT, KCfg<WM, BL>::PMINB)
         const ItemDev &item = s_rec[r];
         const unsigned m = item.meta;
         unsigned char *buf = smem + b * buf_bytes;
-        const bool tma_item = TMA && (m & ITEM_TMA);
+        const bool tma_item = TMA_ONLY || (TMA && (m & ITEM_TMA));
         if (tma_item) {
             // every thread waits (bounded) for the tensor copy; on a timeout it marks the batch
             // failed and goes on, so that no barrier is left unmatched
