@@ -124,7 +124,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true", help="leave the short serving sweep out of the default line")
     p.add_argument("--tune", action="store_true",
                    help="autotune the uniform batch before timing it (its choice on the GB300 equals the library's "
-                        "defaults: prefetching form, 3 CTAs per SM, lag 8, even split); the uneven batch is always tuned")
+                        "defaults: prefetching form, 3 CTAs per SM, lag 32, even split); the uneven batch is always tuned")
     p.add_argument("--no-other-width", action="store_true",
                    help="leave out the uniform batch at the other residue width (60-bit when --bits 124)")
     p.add_argument("--lag", type=int, default=0, help="pipeline lag of the persistent batch (0: library default)")

@@ -58,7 +58,7 @@ typedef struct mq_batch_opts {
     unsigned ctas_per_sm;  /* persistent CTAs per SM (0: as many as fit -- 3 with the prefetching form,
                               4 for batches of 64-bit transforms only; 2 and 3 with the split form;
                               larger values are clamped to that) */
-    unsigned lag;          /* pipeline lag between dependent stages, in waves of the persistent grid (0: 8) */
+    unsigned lag;          /* pipeline lag between dependent stages, in waves of the persistent grid (0: 32) */
     unsigned blas_chunk;   /* residues per BLAS work item (0: 16384); a multiple of 2048 */
     double wait_timeout_s; /* limit of every device-side wait (0: 2 s) */
     unsigned flags;        /* MQ_BATCH_* */

@@ -270,7 +270,7 @@ static bool same_shape(const mq_job &a, const mq_job &b) {
 }
 
 void mq::batch_detail::apply_defaults(mq_batch_opts &o) {
-    if (o.lag == 0) o.lag = 8;
+    if (o.lag == 0) o.lag = 32;  // stage-major for batches up to 32 waves per stage (see the lag sweep)
     if (o.blas_chunk == 0) o.blas_chunk = 16384;
     o.blas_chunk = (o.blas_chunk + 2047) / 2048 * 2048;
     if (o.wait_timeout_s <= 0) o.wait_timeout_s = 2.0;
@@ -882,7 +882,7 @@ extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts
     }
     const unsigned forms[] = {MQ_BATCH_FORM_PREFETCH, MQ_BATCH_FORM_SPLIT};
     const unsigned ctas[] = {1, 2, 3, 4};  // beyond what an instantiation holds, the grid repeats and is skipped
-    const unsigned lags[] = {1, 2, 4, 8};
+    const unsigned lags[] = {1, 2, 4, 8, 16, 32};
     const unsigned chunks[] = {8192, 16384, 65536};
     double best_ms = 1e30;
     mq_batch_opts bo{};
