@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "hostmath.h"
 #include "plan.h"
+#include "trace.h"
 #include "widehost.h"
 
 using namespace mq;
@@ -198,6 +199,7 @@ static int plan_create_wide(ntt_plan **out, unsigned log2n, const uint64_t *q, c
 
 extern "C" int ntt_plan_create(ntt_plan **out, unsigned log2n, const uint64_t q[2], const uint64_t root[2], int width,
                                unsigned flags, void *stream) {
+    MQ_TRACE("ntt_plan_create");
     if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!root) return mq_fail(MQ_ERR_ARG, "root is NULL");
@@ -378,10 +380,12 @@ static int ntt_run(const ntt_plan *p, void *d, size_t batch, size_t stride, void
 }
 
 extern "C" int ntt_forward(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
+    MQ_TRACE("ntt_forward");
     return ntt_run(p, d, batch, stride, stream, false);
 }
 
 extern "C" int ntt_inverse(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
+    MQ_TRACE("ntt_inverse");
     return ntt_run(p, d, batch, stride, stream, true);
 }
 
@@ -391,6 +395,7 @@ extern "C" int ntt_inverse(const ntt_plan *p, void *d, size_t batch, size_t stri
 // column passes run before (a into c, b into scratch) and after it (inverse, N^-1 folded in).
 extern "C" int ntt_polymul(const ntt_plan *p, void *c, const void *a, const void *b, size_t batch, size_t stride,
                            void *stream) {
+    MQ_TRACE("ntt_polymul");
     if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
     if (p->width > MQ_W128) return mq_fail(MQ_ERR_ARG, "the fused product takes residues of one or two words");
     if (batch == 0) return MQ_OK;
@@ -547,16 +552,20 @@ static int blas(int op, void *c, const void *a, const void *b, size_t n, const u
 }
 
 extern "C" int mod_vadd(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    MQ_TRACE("mod_vadd");
     return blas(OP_VADD, c, a, b, n, q, width, nullptr, stream);
 }
 extern "C" int mod_vsub(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    MQ_TRACE("mod_vsub");
     return blas(OP_VSUB, c, a, b, n, q, width, nullptr, stream);
 }
 extern "C" int mod_vmul(void *c, const void *a, const void *b, size_t n, const uint64_t q[2], int width, void *stream) {
+    MQ_TRACE("mod_vmul");
     return blas(OP_VMUL, c, a, b, n, q, width, nullptr, stream);
 }
 extern "C" int mod_axpy(void *y, const uint64_t a[2], const void *x, size_t n, const uint64_t q[2], int width,
                         void *stream) {
+    MQ_TRACE("mod_axpy");
     // y = a*x + y: the kernel's first operand is x, the second (and the output) is y
     return blas(OP_AXPY, y, x, y, n, q, width, a, stream);
 }

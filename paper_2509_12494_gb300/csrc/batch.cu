@@ -34,6 +34,7 @@
 
 #include "../../include/mqntt_batch.h"
 #include "batch_internal.h"
+#include "trace.h"
 #include "batch_kernel.cuh"
 #include "blas_ops.cuh"
 #include "common.cuh"
@@ -578,6 +579,7 @@ static int capture_graph(mq_batch *b) {
 }
 
 extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs, const mq_batch_opts *opts, void *stream) {
+    MQ_TRACE("mq_batch_create");
     if (!out) return mq_fail(MQ_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!jobs || njobs == 0) return mq_fail(MQ_ERR_ARG, "a batch needs at least one job");
@@ -692,6 +694,7 @@ extern "C" int mq_batch_create(mq_batch **out, const mq_job *jobs, size_t njobs,
 }
 
 extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, void *stream) {
+    MQ_TRACE("mq_batch_update");
     if (!b || !jobs) return mq_fail(MQ_ERR_ARG, "NULL batch or jobs");
     if (njobs != b->shape.size()) return mq_fail(MQ_ERR_ARG, "the batch has %zu jobs, got %zu", b->shape.size(), njobs);
     for (size_t i = 0; i < njobs; ++i)
@@ -725,6 +728,7 @@ extern "C" int mq_batch_update(mq_batch *b, const mq_job *jobs, size_t njobs, vo
 }
 
 extern "C" int mq_batch_launch(mq_batch *b, void *stream) {
+    MQ_TRACE("mq_batch_launch");
     if (!b) return mq_fail(MQ_ERR_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
@@ -870,6 +874,7 @@ static int lookup_tuned(const std::vector<mq_job> &jobs, mq_batch_opts &o) {
 }
 
 extern "C" int mq_autotune_batch(const mq_job *jobs, size_t njobs, mq_batch_opts *best, const char *cache_path, void *stream) {
+    MQ_TRACE("mq_autotune_batch");
     if (!jobs || !njobs || !best) return mq_fail(MQ_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     bool has_blas = false, has_deps = false, has_twopass = false, has_check = false;

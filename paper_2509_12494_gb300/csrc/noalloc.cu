@@ -14,6 +14,7 @@
 #include "../../include/mqntt.h"
 #include "common.cuh"
 #include "plan.h"
+#include "trace.h"
 
 int mq_fail(int code, const char *fmt, ...);
 int mq_cuda_fail(cudaError_t e, const char *where);
@@ -63,6 +64,7 @@ static PassArgs noalloc_pass(const ntt_plan *p, size_t batch) {
 }
 
 extern "C" int ntt_forward_noalloc(const ntt_plan *p, void *d, size_t batch, size_t stride, void *stream) {
+    MQ_TRACE("ntt_forward_noalloc");
     if (!p) return mq_fail(MQ_ERR_ARG, "plan is NULL");
     if (p->flags & MQ_CHECK_INPUTS)
         return mq_fail(MQ_ERR_ARG, "ntt_forward_noalloc does not run the input check: use a plan without MQ_CHECK_INPUTS");

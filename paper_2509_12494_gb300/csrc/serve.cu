@@ -31,6 +31,7 @@
 #include "../../include/mqntt_serve.h"
 #include "batch_internal.h"
 #include "plan.h"
+#include "trace.h"
 
 int mq_fail(int code, const char *fmt, ...);
 int mq_cuda_fail(cudaError_t e, const char *where);
@@ -258,6 +259,7 @@ int grow(Slot *sl, size_t njobs, size_t nitems, size_t nctrs) {
 
 // Build and launch one batch of requests on a free slot (called without the server lock).
 int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
+    MQ_TRACE("mq_server batch");
     const size_t n = jobs.size();
     std::vector<void *> scratch(n, nullptr);
     int rc = MQ_OK;
@@ -300,6 +302,7 @@ int launch_batch(Server *s, Slot *sl, std::vector<mq_job> &jobs) {
 }
 
 int run_plain(Server *s, uint64_t id) {
+    MQ_TRACE("mq_server plain request");
     const mq_job &j = s->ticket(id).job;
     void *st = (void *)s->plain_stream;
     if (job_scratch_bytes(j) && s->take_injected_failure())
