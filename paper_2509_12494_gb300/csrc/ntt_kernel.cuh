@@ -641,7 +641,11 @@ __global__ void __launch_bounds__(256, 3)
         }
         __syncthreads();
         if (!s_ok) {
-            if (tid == 0) atomicCAS(&g_tma_fault, 0ull, grp + 1);
+            if (tid == 0) {  // record the fault, then wait (bounded again) for the copies in flight
+                atomicCAS(&g_tma_fault, 0ull, grp + 1);
+                tma::mbar_wait(bc, ph, TMA_WAIT_NS);
+                if (next < groups) tma::mbar_wait(bn, odd ? ph0 : ph1, TMA_WAIT_NS);
+            }
             break;
         }
         while (!tma::mbar_test(bc, ph)) {  // completed: thread 0 saw it

@@ -111,7 +111,10 @@ __global__ void __launch_bounds__(256, 3)
         }
         __syncthreads();
         if (!s_ok) {
-            if (tid == 0) atomicCAS(&ntt_detail::g_tma_fault, 0ull, grp + 1);
+            if (tid == 0) {  // record the fault, then wait (bounded again) for the copies in flight
+                atomicCAS(&ntt_detail::g_tma_fault, 0ull, grp + 1);
+                tma::mbar_wait(&bar, ph, ntt_detail::TMA_WAIT_NS);
+            }
             break;
         }
         while (!tma::mbar_test(&bar, ph)) {  // completed: thread 0 saw it
