@@ -34,7 +34,7 @@ struct JobDev {
     PassArgs pa[2];            // NTT passes
     BlasArgs ba;               // BLAS operands
     int tma[2];                // pass p takes the TMA form (tma.cuh); its tensor maps follow
-    alignas(64) CUtensorMap tm[2][2];  // [pass][0: source, 1: destination]
+    CUtensorMap tm[2][2];      // [pass][0: source, 1: destination]; 128-byte aligned by their type
 };
 
 // One work item (32 bytes; the prefetching kernel copies it into shared memory with two 16-byte
